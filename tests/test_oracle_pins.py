@@ -1,0 +1,382 @@
+"""Pins of the CPU oracle against things other than itself (no GPU needed).
+
+Each test fixes the oracle to something the paper or the mathematics fixes:
+the paper's worked examples (Sec. 5), exact rational arithmetic, closed forms,
+brute-force binary128 Jacobi on tiny matrices, high-precision mpmath, and the
+invariants of a symmetric eigen-decomposition (interlacing, trace, residual,
+orthogonality).  A dropped term, a wrong sign or a transposed index anywhere in
+the oracle's secular functions or vector formulas fails one of them.
+"""
+from decimal import Decimal, getcontext
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1302_7203_gb300 import workloads as W
+from conftest import read_golden
+
+EPS = 2.0 ** -53
+
+
+def arrow_dense(d, z, alpha):
+    n = len(d) + 1
+    A = np.zeros((n, n))
+    A[np.arange(n - 1), np.arange(n - 1)] = d
+    A[:-1, -1] = z
+    A[-1, :-1] = z
+    A[-1, -1] = alpha
+    return A
+
+
+def arrow_matvec(d, z, alpha, V):
+    """A @ V without forming A."""
+    out = np.empty_like(V)
+    out[:-1] = d[:, None] * V[:-1] + z[:, None] * V[-1][None, :]
+    out[-1] = z @ V[:-1] + alpha * V[-1]
+    return out
+
+
+# ----------------------------------------------------------------------------
+# double-double primitives against exact rationals
+# ----------------------------------------------------------------------------
+def test_dd_primitives_exact_rationals():
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        ah, bh = rng.standard_normal(2) * 10.0 ** rng.integers(-30, 30, 2)
+        al = ah * 2.0 ** -60 * rng.standard_normal()
+        bl = bh * 2.0 ** -60 * rng.standard_normal()
+        a = Fraction(ah) + Fraction(al)
+        b = Fraction(bh) + Fraction(bl)
+        (s, sl), (p, pl), (q, ql), (r, rl) = oracle.dd_ops(ah, al, bh, bl)
+        for got, exact in (((s, sl), a + b), ((p, pl), a * b), ((q, ql), a / b)):
+            g = Fraction(got[0]) + Fraction(got[1])
+            if exact != 0:
+                assert abs((g - exact) / exact) < Fraction(2) ** -100
+        # sqrt: (r + rl)^2 vs |a|
+        g = Fraction(r) + Fraction(rl)
+        assert abs((g * g - abs(a)) / abs(a)) < Fraction(2) ** -98
+
+
+# ----------------------------------------------------------------------------
+# the paper's worked examples (Sec. 5)
+# ----------------------------------------------------------------------------
+def test_example1_eigenvalues_and_vector():
+    d, z, a = W.paper_example(1)
+    r = oracle.arrow_eig(d, z, a)
+    rows = read_golden("example1.txt")
+    lam_ref = [float(v[0]) for k, v in rows if k == "lambda"]
+    v4_ref = np.array([float(v[0]) for k, v in rows if k == "v4"])
+    # 16 printed digits: relative 5e-16 from the print, plus the oracle's own error
+    np.testing.assert_allclose(r["lam"], lam_ref, rtol=6e-16, atol=0)
+    v4 = r["V"][:, 3]
+    # the paper's v_4 has the opposite global sign (x_n = -1 convention, Eq. Aeigenvec)
+    np.testing.assert_allclose(-v4, v4_ref, rtol=2e-15, atol=0)
+    assert v4[-1] < 0  # x_n = -1 convention
+    assert np.all(r["relerr"] < 2.0 ** -80)
+
+
+def test_example2_32_digits():
+    d, z, a = W.paper_example(2)
+    r = oracle.arrow_eig(d, z, a)
+    rows = read_golden("example2.txt")
+    getcontext().prec = 50
+    l32 = [(Decimal(v[0]), Decimal(v[1])) for k, v in rows if k == "lambda32"]
+    l16 = [Decimal(v[0]) for k, v in rows if k == "lambda16"]
+    for i, (printed, corrected) in enumerate(l32):
+        got = Decimal(float(r["lam"][i])) + Decimal(float(r["lam_lo"][i]))
+        assert abs(got - corrected) / abs(corrected) < Decimal("2e-30"), i
+        if printed != corrected:   # the misprinted digits are far beyond double
+            assert abs(got - printed) / abs(printed) < Decimal("3e-19"), i
+    # rounded to double, the interior eigenvalues equal Algorithm 5's printed
+    # output; the exterior ones are within the one ulp the printed run was off
+    for i, v in enumerate(l16):
+        got = Decimal(float(r["lam"][i]))
+        if i in (1, 2, 3):
+            assert float(got) == float(v), i
+        else:
+            printed = float(v)        # the double that the 16-digit print denotes
+            assert abs(float(got) - printed) <= np.spacing(abs(printed)), i
+    # Remark 1a: the pairs (d_i, mu) represent lambda_2..lambda_4 to ~32 digits
+    for i in (1, 2, 3):
+        rep = Decimal(float(r["sigma"][i])) + Decimal(float(r["mu_hi"][i])) \
+            + Decimal(float(r["mu_lo"][i]))
+        assert abs(rep - l32[i][1]) < Decimal("1e-30")
+
+
+def test_example3_eigenvalues_b_and_conditions():
+    d, z, a = W.paper_example(3)
+    r = oracle.arrow_eig(d, z, a)
+    rows = read_golden("example3.txt")
+    lam_ref = [float(v[0]) for k, v in rows if k == "lambda"]
+    np.testing.assert_allclose(r["lam"], lam_ref, rtol=6e-16, atol=0)
+    # b of A_2^-1 (shift to d_2 = 4) by definition, in double-double
+    b_doubled = [float(v[0]) for k, v in rows if k == "b_doubled"][0]
+    b_hi, b_lo, kb = oracle.inverse_element(d, z, a, 1)
+    assert b_hi == b_doubled
+    b_std = [float(v[0]) for k, v in rows if k == "b_standard"][0]
+    assert abs(b_hi - b_std) > 1e-9   # the standard-precision value is wrong
+    # K_b (Eq. K2) for shifts d_2..d_5 and K_nu (Eq. K0) for eigenvalues 2..6
+    lam = [Fraction(float(x)) + Fraction(float(y)) for x, y in zip(r["lam"], r["lam_lo"])]
+    table = [(int(v[0]), float(v[1]), float(v[2])) for k, v in rows if k == "knu_kb"]
+    for row, (pole1, knu_ref, kb_ref) in enumerate(table):
+        i = pole1 - 1
+        _, _, kb = oracle.inverse_element(d, z, a, i)
+        assert abs(kb - kb_ref) / kb_ref < 3e-7
+        k = row + 1                              # eigenvalue index (0-based)
+        di = Fraction(float(d[i]))
+        mu = abs(lam[k] - di)
+        # eigenvalues of A - d_i I nearest zero on either side: lambda_i and lambda_{i+1}
+        near = min(abs(lam[i] - di), abs(lam[i + 1] - di))
+        knu = float(mu / near)
+        assert abs(knu - knu_ref) / knu_ref < 1e-6
+
+
+# ----------------------------------------------------------------------------
+# closed form, n = 2
+# ----------------------------------------------------------------------------
+def test_closed_form_order_two():
+    getcontext().prec = 60
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        dd_, zz, aa = rng.standard_normal(3) * 10.0 ** rng.integers(-8, 8, 3)
+        r = oracle.arrow_eig([dd_], [zz], aa)
+        D, Z, A = Decimal(dd_), Decimal(zz), Decimal(aa)
+        half = (D + A) / 2
+        rad = (((D - A) / 2) ** 2 + Z * Z).sqrt()
+        big = half + rad if half >= 0 else half - rad
+        small = (D * A - Z * Z) / big      # product of the eigenvalues = det
+        ref = sorted([big, small], reverse=True)
+        for i in range(2):
+            got = Decimal(float(r["lam"][i])) + Decimal(float(r["lam_lo"][i]))
+            assert abs(got - ref[i]) <= abs(ref[i]) * Decimal("1e-28")
+        # vector: x = [z/(d - lambda); -1]
+        for i in range(2):
+            x0 = Z / (D - ref[i])
+            nrm = (x0 * x0 + 1).sqrt()
+            assert abs(float(x0 / nrm) - r["V"][0, i]) <= 4e-16 * abs(float(x0 / nrm))
+            assert abs(float(-1 / nrm) - r["V"][1, i]) <= 4e-16 * abs(float(1 / nrm))
+
+
+def test_order_one():
+    r = oracle.arrow_eig(np.zeros(0), np.zeros(0), 3.5)
+    assert r["lam"][0] == 3.5 and r["V"][0, 0] == -1.0
+
+
+# ----------------------------------------------------------------------------
+# brute force: binary128 Jacobi on tiny random matrices
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(12))
+def test_against_binary128_jacobi(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 14))
+    d = np.sort(rng.uniform(-5, 5, n - 1))[::-1]
+    z = rng.standard_normal(n - 1)
+    a = float(rng.standard_normal() * 3)
+    r = oracle.arrow_eig(d, z, a)
+    hi, lo, Vj = oracle.jacobi_sym(arrow_dense(d, z, a))
+    normA = np.abs(arrow_dense(d, z, a)).sum()
+    # Jacobi is absolutely accurate to ~n 2^-113 ||A||
+    assert np.all(np.abs((r["lam"] - hi) + (r["lam_lo"] - lo)) <= 1e-30 * normA)
+    for k in range(n):
+        v = r["V"][:, k]
+        vj = Vj[:, k] * np.sign(Vj[-1, k]) * -1.0       # x_n = -1 convention
+        big = np.abs(vj) > 1e-12
+        np.testing.assert_allclose(v[big], vj[big], rtol=1e-14, atol=1e-30)
+
+
+def test_graded_tiny_against_mpmath():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 80
+    for seed in range(4):
+        d, z, a = W.graded_arrow(9, seed=200 + seed)
+        r = oracle.arrow_eig(d, z, a)
+        n = len(d) + 1
+        A = mp.matrix(n, n)
+        for i in range(n - 1):
+            A[i, i] = mp.mpf(d[i]); A[i, n - 1] = A[n - 1, i] = mp.mpf(z[i])
+        A[n - 1, n - 1] = mp.mpf(a)
+        E, Q = mp.eigsy(A)
+        ev = sorted([E[i] for i in range(n)], reverse=True)
+        for k in range(n):
+            got = mp.mpf(float(r["lam"][k])) + mp.mpf(float(r["lam_lo"][k]))
+            assert abs(got - ev[k]) <= abs(ev[k]) * mp.mpf("1e-26"), (seed, k)
+        # vectors: x_r = z_r/(d_r - lambda) evaluated at 80 digits
+        for k in range(n):
+            x = [mp.mpf(z[i]) / (mp.mpf(d[i]) - ev[k]) for i in range(n - 1)] + [mp.mpf(-1)]
+            nr = mp.sqrt(sum(t * t for t in x))
+            for i in range(n):
+                ref = float(x[i] / nr)
+                assert abs(r["V"][i, k] - ref) <= 3e-16 * abs(ref), (seed, k, i)
+
+
+# ----------------------------------------------------------------------------
+# invariants at a realistic size
+# ----------------------------------------------------------------------------
+def test_invariants_uniform_n1000():
+    n = 1000
+    d, z, a = W.uniform_arrow(n, seed=0)
+    r = oracle.arrow_eig(d, z, a)
+    lam, V = r["lam"], r["V"]
+    # strict interlacing lambda_1 > d_1 > lambda_2 > ... > d_{n-1} > lambda_n (Eq. interlace)
+    assert np.all(lam[:-1] > d) and np.all(d > lam[1:])
+    # trace
+    tr = np.sum(np.array([Fraction(x) + Fraction(y) for x, y in zip(lam, r["lam_lo"])]))
+    ref = sum(Fraction(x) for x in d) + Fraction(a)
+    assert abs(float(tr - ref)) <= 1e-25 * np.abs(lam).sum()
+    # residual and orthogonality at working precision
+    normA = np.abs(d).max() + np.linalg.norm(z) + abs(a)
+    res = arrow_matvec(d, z, a, V) - V * lam[None, :]
+    assert np.abs(res).max() <= 4 * EPS * normA
+    G = V.T @ V - np.eye(n)
+    assert np.abs(G).max() <= 2 * n * EPS
+    assert np.all(V[-1] < 0)
+    assert np.all(r["relerr"] < 2.0 ** -70)
+
+
+def test_graded_invariants_and_self_bound():
+    n = 600
+    d, z, a = W.graded_arrow(n, seed=1)
+    r = oracle.arrow_eig(d, z, a)
+    lam = r["lam"]
+    assert np.all(lam[:-1] >= d) and np.all(d >= lam[1:])
+    assert np.all(r["relerr"] < 2.0 ** -60)
+    V = r["V"]
+    G = V.T @ V - np.eye(n)
+    assert np.abs(G).max() <= 2 * n * EPS
+
+
+def test_against_numpy_eigh():
+    n = 300
+    d, z, a = W.uniform_arrow(n, seed=9)
+    r = oracle.arrow_eig(d, z, a, vectors=False)
+    ev = np.linalg.eigvalsh(arrow_dense(d, z, a))[::-1]
+    normA = np.linalg.norm(arrow_dense(d, z, a), 2)
+    assert np.abs(r["lam"] - ev).max() <= 50 * n * EPS * normA
+
+
+def test_mirrored_spectrum_symmetric():
+    n = 41
+    d, z, a = W.mirrored_arrow(n)
+    r = oracle.arrow_eig(d, z, a)
+    lam = r["lam"]
+    scale = np.abs(lam).max()
+    assert np.all(np.abs(lam + lam[::-1]) <= 1e-28 * scale)
+    assert abs(lam[n // 2]) <= 1e-28 * scale
+
+
+def test_sampled_outputs_match_full():
+    n = 400
+    d, z, a = W.graded_arrow(n, seed=3)
+    full = oracle.arrow_eig(d, z, a)
+    ks = np.array([0, 5, 199, 200, 398, 399])
+    part = oracle.arrow_eig(d, z, a, ks=ks)
+    np.testing.assert_array_equal(part["lam"], full["lam"][ks])
+    np.testing.assert_array_equal(part["V"], full["V"][:, ks])
+
+
+# ----------------------------------------------------------------------------
+# reduction (Sec. 1): zero spikes, equal poles, ordering, signs
+# ----------------------------------------------------------------------------
+def test_reduction_decisions_by_hand():
+    d = np.array([1.0, 3.0, 2.0, 3.0, -1.0, 3.0, 2.0])
+    z = np.array([0.5, -1.0, 0.0, 2.0, 1.0, -0.0, 0.25])
+    order, kind, head, m = oracle.reduce(d, z)
+    # stable descending: 3.0 (rows 1,3,5), 2.0 (rows 2,6), 1.0 (row 0), -1.0 (row 4)
+    assert list(order) == [1, 3, 5, 2, 6, 0, 4]
+    # rows 2 and 5 have zero spikes (+0 and -0); row 3 folds into row 1
+    assert list(kind) == [0, 0, 1, 2, 0, 1, 0]
+    assert head[3] == 1 and head[1] == 1 and head[6] == 6
+    assert m == 4
+
+
+def test_deflation_matches_dense_jacobi():
+    d = np.array([3.0, 2.0, 2.0, 1.0, 2.0, 0.5, -1.0])
+    z = np.array([1.0, -0.5, 0.75, 0.0, 2.0, -1.5, 0.3])
+    a = 0.7
+    r = oracle.arrow_eig(d, z, a)
+    A = arrow_dense(d, z, a)
+    hi, lo, _ = oracle.jacobi_sym(A)
+    np.testing.assert_allclose(r["lam"], hi, rtol=1e-15, atol=1e-15)
+    V = r["V"]
+    n = len(d) + 1
+    np.testing.assert_allclose(V.T @ V, np.eye(n), atol=1e-15)
+    np.testing.assert_allclose(A @ V, V * r["lam"][None, :], atol=4e-15)
+    # the zero-spike row 3 gives (d_3, e_3)
+    k = np.nonzero(np.all(np.abs(V - np.eye(n)[:, [3]]) < 1e-300, axis=0))[0]
+    assert k.size == 1 and r["lam"][k[0]] == 1.0
+
+
+def test_sign_flip_flips_rows():
+    d, z, a = W.uniform_arrow(50, seed=4)
+    r1 = oracle.arrow_eig(d, z, a)
+    z2 = z.copy()
+    z2[[3, 17]] *= -1
+    r2 = oracle.arrow_eig(d, z2, a)
+    np.testing.assert_array_equal(r1["lam"], r2["lam"])
+    V1 = r1["V"].copy()
+    V1[[3, 17]] *= -1
+    np.testing.assert_array_equal(V1, r2["V"])
+
+
+# ----------------------------------------------------------------------------
+# DPR1 and triangular-arrowhead SVD (Sec. 6.2, 6.3)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("rho", [0.5, 2.0, -0.75])
+def test_dpr1_against_jacobi(rho):
+    rng = np.random.default_rng(21)
+    for n in (2, 5, 11):
+        # dyadic grid, so that the dense D + rho u u^T below is formed exactly
+        d = np.sort(rng.choice(2 ** 20, n, replace=False) / 2.0 ** 20)[::-1]
+        u = rng.integers(-1023, 1024, n) / 2.0 ** 10
+        u[u == 0] = 1.0 / 2 ** 10
+        r = oracle.dpr1_eig(d, u, rho)
+        M = np.diag(d) + rho * np.outer(u, u)
+        hi, lo, Vj = oracle.jacobi_sym(M)
+        np.testing.assert_allclose(r["lam"], hi, rtol=1e-15, atol=1e-16)
+        Q = r["Q"]
+        np.testing.assert_allclose(Q.T @ Q, np.eye(n), atol=2e-15)
+        np.testing.assert_allclose(M @ Q, Q * r["lam"][None, :], atol=4e-15)
+        # convention: q ~ (D - lambda I)^{-1} u with a positive factor
+        for k in range(n):
+            y = u / (d - r["lam"][k])
+            assert np.dot(y, Q[:, k]) > 0
+
+
+def test_dpr1_interlacing_uniform():
+    d, u, rho = W.uniform_dpr1(300, seed=3)
+    r = oracle.dpr1_eig(d, u, rho, vectors=False)
+    lam = r["lam"]
+    assert np.all(lam > d) and np.all(lam[1:] < d[:-1])   # lambda_k in (d_k, d_{k-1})
+    assert abs(lam.sum() - (d.sum() + rho * (u @ u))) <= 1e-13
+
+
+def test_tsvd_against_jacobi_svd():
+    rng = np.random.default_rng(31)
+    for n in (2, 4, 9):
+        d, z, a = W.uniform_tsvd(n, seed=int(rng.integers(1000)))
+        r = oracle.tsvd(d, z, a)
+        B = np.zeros((n, n))
+        B[np.arange(n - 1), np.arange(n - 1)] = d
+        B[:-1, -1] = z
+        B[-1, -1] = a
+        s, Uj, Vj = oracle.jacobi_svd(B)
+        np.testing.assert_allclose(r["s"], s, rtol=1e-15)
+        U, V = r["U"], r["V"]
+        np.testing.assert_allclose(B @ V, U * r["s"][None, :], atol=4e-15)
+        np.testing.assert_allclose(U.T @ U, np.eye(n), atol=4e-15)
+        np.testing.assert_allclose(V.T @ V, np.eye(n), atol=4e-15)
+        assert np.all(V[-1] < 0)
+
+
+def test_tsvd_against_numpy_svd():
+    n = 200
+    d, z, a = W.uniform_tsvd(n, seed=4)
+    r = oracle.tsvd(d, z, a, vectors=False)
+    B = np.zeros((n, n))
+    B[np.arange(n - 1), np.arange(n - 1)] = d
+    B[:-1, -1] = z
+    B[-1, -1] = a
+    s = np.linalg.svd(B, compute_uv=False)
+    assert np.abs(r["s"] - s).max() <= 20 * n * EPS * s[0]
