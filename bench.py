@@ -1,0 +1,278 @@
+#!/usr/bin/env python
+"""Benchmark of the GPU arrowhead eigen-solver (one JSON line on rank 0).
+
+Workload: the graded arrowhead of order n = 16384 (|d| = 10^U[-15,0] with random
+signs, z = 10^U[-10,0], alpha = 1e3), all n eigenpairs with the full n x n
+eigenvector matrix in FP64.  One step = one complete arrow_eig call (reduction,
+shift-and-invert bisection for every eigenvalue, remedies, vectors).
+
+value      eigenpairs/s of the whole job, inputs resident in HBM, device time of
+           exactly K steps (CUDA events on the solve stream), max over ranks.
+           Between steps a 512 MiB buffer is written to flush L2 (129 MB).
+e2e        the same metric through arrow_eig_host: pinned host d, z in, lambda
+           and V (2 GiB) out, copies inside the timed region.
+roofline   the eigenvalue kernel (k_eig): algorithmic FP64 flops per launch
+           (3 per term per bisection step: subtract, divide, add, as in
+           Algorithm 3; 3 per term for the shift choice; 20 per term for the
+           double-double element b) over its event-timed duration, against the
+           FP64 ALU peak 152 SMs x 4 flop/clk x 2070 MHz.
+cpu_baseline  the CPU oracle on a bounded sample of eigenpairs of the same
+           matrix, on all host cores.
+--impl reference   times the CPU oracle alone (the reference arm).
+Multi-GPU (torchrun): each rank solves its own instance (weak scaling, no
+collective on the data path).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "eigenpairs/s at ≤10nε64 rel. err (n=16384, batched); p50/p99 solve latency"
+UNIT = "eigenpairs/s"
+N_DEFAULT = 16384
+LAUNCHES_PER_STEP = 8   # k_check k_rank k_reduce k_eig k_fix_decide k_fix_solve k_place k_vectors
+FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def eig_kernel_flops(n, ncomp, total_iter, fix_iter):
+    """Algorithmic FP64 flops of one k_eig launch (see module docstring)."""
+    terms = n - 2                    # each O(n) pass runs over the other poles
+    return 3.0 * terms * (total_iter - fix_iter) + (3.0 + 20.0) * terms * ncomp
+
+
+def cpu_baseline(d, z, alpha, n, seconds):
+    import oracle
+    oracle.build_oracle()
+    # size the sample from a short calibration run
+    ks = np.linspace(0, n - 1, 16).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.arrow_eig(d, z, alpha, ks=ks)
+    per = (time.perf_counter() - t0) / ks.size
+    cnt = int(max(16, min(n, seconds / max(per, 1e-9))))
+    ks = np.unique(np.linspace(0, n - 1, cnt).astype(np.int64))
+    t0 = time.perf_counter()
+    oracle.arrow_eig(d, z, alpha, ks=ks)
+    dt = time.perf_counter() - t0
+    return {"value": ks.size / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{ks.size} of {n} eigenpairs (evenly spaced) with vectors, "
+                      f"double-double oracle, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle, timed on the host cores."""
+    if rank != 0:
+        return
+    from paper_1302_7203_gb300 import workloads as W
+    import oracle
+    oracle.build_oracle()
+    n = args.n
+    d, z, alpha = W.graded_arrow(n, seed=1)
+    per_step = max(8, int(args.cpu_seconds * 4 / max(args.steps + args.warmup, 1)))
+    ks0 = np.linspace(0, n - 1, per_step).astype(np.int64)
+    for _ in range(args.warmup):
+        oracle.arrow_eig(d, z, alpha, ks=ks0[:8])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        ks = np.unique((ks0 + s) % n)
+        oracle.arrow_eig(d, z, alpha, ks=ks)
+    dt = time.perf_counter() - t0
+    done = per_step * args.steps
+    val = done / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (double-double oracle)",
+            "data": "synthetic",
+            "config": {"workload": f"graded arrowhead n={n} (seed 1), sampled eigenpairs "
+                                   "with vectors", "n": n},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.threads(),
+                             "kind": "oracle",
+                             "sample": f"{per_step} eigenpairs per step of {n}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_1302_7203_gb300 import arrowhead, build, workloads as W
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    d, z, alpha = W.graded_arrow(n, seed=1 + rank)
+    dev = torch.device("cuda", local)
+    dt = torch.as_tensor(d, device=dev)
+    zt = torch.as_tensor(z, device=dev)
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    V = torch.empty((n, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    prec = arrowhead.AE_FP64 if args.precision == "fp64" else arrowhead.AE_FP32_BRACKET
+    opts = arrowhead.default_opts(precision=prec, profile=1)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return arrowhead.arrow_eig(dt, zt, alpha, opts=opts, info=True,
+                                   out={"lam": lam, "V": V}, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    infos = []
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)                 # evict L2 between steps
+            starts[i].record(stream)
+            infos.append(step()["info"])
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * args.steps / (total_ms / 1e3)
+    info = infos[-1]
+    eig_ms = float(np.mean([x["ms_eig"] for x in infos]))
+    flops = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"])
+    achieved = flops / (eig_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "kernel": "k_eig", "kernel_ms": eig_ms,
+            "peak_note": "FP64 ALU: 152 SMs x 4 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)"}
+
+    e2e = None
+    if not args.no_e2e:
+        dh = torch.as_tensor(d).pin_memory()
+        zh = torch.as_tensor(z).pin_memory()
+        lh = torch.empty(n, dtype=torch.float64).pin_memory()
+        Vh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        arrowhead.arrow_eig_host(dh, zh, alpha, out={"lam": lh, "V": Vh}, stream=stream)
+        t0 = time.perf_counter()
+        ne = max(2, min(args.steps, 3))
+        for _ in range(ne):
+            arrowhead.arrow_eig_host(dh, zh, alpha, out={"lam": lh, "V": Vh}, stream=stream)
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * n * ne / te, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * (n - 1) * 8, "d2h_bytes_per_step": (n + n * n) * 8}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            cpu = cpu_baseline(d, z, alpha, n, args.cpu_seconds)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"graded arrowhead n={n}: all eigenpairs + full V",
+                           "n": n, "precision": args.precision,
+                           "l2": "512 MiB write between steps (L2 flush)",
+                           "parallelism": f"{world} independent instances"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+                "clocks": clk.summary(), "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+                "phases_ms": {k: float(np.mean([x[k] for x in infos]))
+                              for k in ("ms_reduce", "ms_eig", "ms_fix", "ms_vectors")},
+                "solver": {k: info[k] for k in ("n_nearzero", "n_otherpole", "n_dpr1shift",
+                                                "n_capped", "max_iter_used", "total_iter",
+                                                "fix_iter", "max_Kb", "max_Knu")}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

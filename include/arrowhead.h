@@ -1,0 +1,166 @@
+/*
+ * arrowhead.h -- C ABI of the GB300 arrowhead eigen-solver library
+ * (libarrowhead.so, built for sm_103a).
+ *
+ * Method: Jakovcevic Stor, Slapnicar & Barlow, "Accurate eigenvalue
+ * decomposition of arrowhead matrices and applications".  For each eigenvalue
+ * the solver shifts to the nearest pole d_i (Algorithm 1), forms the inverse of
+ * the shifted arrowhead (Eq. invAi) with its one cancellation-prone element b
+ * (Eq. b_ob) in double-double arithmetic (Theorem 6), finds that inverse's
+ * extreme eigenvalue nu by bisection (Algorithm 3), and returns
+ * lambda = d_i + 1/nu with the eigenvector of Eq. (eigenvecAi) / Algorithm 4.
+ * Eigenvalues whose shifted value cancels (the special cases after Theorem C1)
+ * are recomputed from the inverse of A (Remark 1); eigenvalues with a large
+ * K_nu (Eq. K0) are recomputed from another pole or a DPR1 inverse (Remark 2).
+ *
+ * Conventions shared by every entry point:
+ *  - All array arguments are DEVICE pointers (cudaMalloc'd, managed or
+ *    device-accessible), owned by the caller, unless the name ends in _host.
+ *  - All work is issued on `stream` (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream) and is asynchronous: outputs are valid once
+ *    the stream has completed.  Inputs must stay unchanged until then.
+ *  - Matrices are column-major with a leading dimension; column k pairs with
+ *    the k-th eigen/singular value.  Rows are in the caller's input order.
+ *  - The library allocates its O(n) scratch with cudaMallocAsync on `stream`
+ *    and frees it the same way; nothing is kept between calls.
+ *  - Return value: AE_OK (0); -k when argument k (1-based) is invalid
+ *    (LAPACK convention); AE_ERR_* (> 1000) for CUDA or device-side failures.
+ *    When `info` is non-NULL the call waits for the stream and fills it, and
+ *    device-side conditions (non-finite input, iteration cap reached) are
+ *    reported in the return value as well; with info == NULL the call does
+ *    not synchronise and such conditions show up only as NaN outputs.
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef ARROWHEAD_H
+#define ARROWHEAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AE_OK 0
+#define AE_ERR_CUDA 1001      /* a CUDA runtime call failed (see ae_last_cuda_error) */
+#define AE_ERR_INPUT 1002     /* device-side check: non-finite d, z or alpha */
+#define AE_ERR_NOCONV 1003    /* some eigenpair reached opts->max_iter */
+
+/* precision of the bisection (see ae_opts.precision) */
+#define AE_FP64 0             /* all-FP64 bisection from the Gershgorin bracket */
+#define AE_FP32_BRACKET 1     /* FP32 opening bracket, verified and finished in FP64 */
+
+/* per-eigenpair flag bits reported through ae_diag.flags */
+#define AE_FLAG_DEFLATED 1    /* deflated by the reduction (zero spike / equal pole) */
+#define AE_FLAG_NEARZERO 2    /* recomputed from A^{-1} (Remark 1) */
+#define AE_FLAG_OTHERPOLE 4   /* recomputed shifted to the other pole (Remark 2a) */
+#define AE_FLAG_DPR1SHIFT 8   /* recomputed from (A - sigma I)^{-1} (Remark 2b) */
+#define AE_FLAG_CAPPED 16     /* bisection stopped at max_iter */
+#define AE_FLAG_SINGULAR 32   /* remedy found a zero denominator: lambda = sigma */
+#define AE_FLAG_FP32_FALLBACK 64 /* FP32 bracket failed its FP64 check */
+
+typedef struct ae_opts {
+    int precision;     /* AE_FP64 (default) or AE_FP32_BRACKET */
+    double knu_max;    /* K_nu above which Remark 2 is applied; default 10 */
+    int max_iter;      /* bisection iteration cap per eigenpair; default 2200 */
+    int fixup;         /* 1 (default): Remarks 1 and 2; 0: Algorithm 1 only */
+    int profile;       /* 1: time the phases with CUDA events recorded on the
+                          call's stream; the times land in ae_info (default 0) */
+} ae_opts;
+
+/* Summary counters, filled on the host when passed (forces a stream sync). */
+typedef struct ae_info {
+    int n_reduced;        /* eigenpairs solved by bisection (m + 1 for arrow_eig) */
+    int n_deflated;       /* eigenpairs returned by the reduction */
+    int n_nearzero;       /* Remark 1 recomputations */
+    int n_otherpole;      /* Remark 2(a) recomputations */
+    int n_dpr1shift;      /* Remark 2(b) recomputations */
+    int n_capped;         /* eigenpairs that hit max_iter */
+    int n_fp32_fallback;  /* FP32 brackets rejected by the FP64 check */
+    int max_iter_used;    /* largest bisection count of any eigenpair */
+    long long total_iter; /* sum of bisection counts (FP64 evaluations) */
+    long long fix_iter;   /* the part of total_iter spent in remedies */
+    double max_Kb;        /* largest K_b of Eq. (K2) met */
+    double max_Knu;       /* largest K_nu of Eq. (K0) met (before remedies) */
+    float ms_reduce;      /* with opts->profile: checks, ordering, reduction */
+    float ms_eig;         /* eigenvalue kernel (shift, b, bisection) */
+    float ms_fix;         /* remedy decisions and recomputations */
+    float ms_vectors;     /* placement and eigenvector columns */
+} ae_info;
+
+/* Optional per-eigenpair diagnostics (device arrays of length n, any may be
+   NULL), indexed like the returned eigenvalues. */
+typedef struct ae_diag {
+    double *b;       /* element b of Eq. (b_ob) used by the final solve (NaN if none) */
+    double *Kb;      /* K_b of Eq. (K2) for the shift pole */
+    double *Knu;     /* K_nu of Eq. (K0) estimated from the neighbouring eigenvalues */
+    int *iters;      /* FP64 bisection steps of the final solve */
+    int *flags;      /* AE_FLAG_* bits */
+} ae_diag;
+
+/* Fill *opts with the defaults above. */
+void ae_default_opts(ae_opts *opts);
+
+/* Human-readable text for a return code. */
+const char *ae_status_string(int status);
+
+/* Text of the last CUDA error seen by the library in this thread. */
+const char *ae_last_cuda_error(void);
+
+/*
+ * arrow_eig -- all eigenpairs of the real symmetric arrowhead matrix
+ *     A = [diag(d) z; z^T alpha]                         (Sec. 1, Eq. A)
+ * of order n (d and z have n - 1 entries).
+ *
+ *  n       matrix order, n >= 1                                        (arg 1)
+ *  d, z    device, n-1 doubles each: poles and spikes in ANY order and sign;
+ *          zero spikes (+0 or -0) and exactly equal poles are deflated
+ *          (Sec. 1): stable descending sort (ties by lower input index),
+ *          zero-spike rows return (d_r, e_r), equal-pole rows are folded
+ *          into the first of their run by rotations              (args 2, 3)
+ *  alpha   the corner element                                          (arg 4)
+ *  lambda  device, n doubles out: eigenvalues in descending order; ties
+ *          between a deflated and a computed value put the deflated first (5)
+ *  V       device, ldv*n doubles out or NULL: column k is the unit
+ *          eigenvector of lambda[k].  A computed eigenpair has
+ *          v = x/||x||, x = [(D - lambda I)^{-1} z ; -1] (Eq. Aeigenvec), so its
+ *          last component is negative.  A zero-spike row r gives e_r; the
+ *          m-th later member q_m of a run of equal poles (nonzero spikes
+ *          z_{q_0..q_t} in input order) gives
+ *          (-z_{q_m} sum_{l<m} z_{q_l} e_{q_l} + R_{m-1}^2 e_{q_m}) / (R_{m-1} R_m),
+ *          R_m^2 = sum_{l<=m} z_{q_l}^2                                (arg 6)
+ *  ldv     leading dimension of V, >= n                                (arg 7)
+ *  shift, mu  device, n doubles out or NULL: lambda[k] = shift[k] + mu[k]
+ *          with shift[k] the pole used (Remark 1a), or the non-pole shift of
+ *          Remarks 1/2(b); deflated values have mu = 0           (args 8, 9)
+ *  opts    NULL for defaults                                          (arg 10)
+ *  info    host, NULL or filled (synchronises)                        (arg 11)
+ *  diag    host struct of optional device arrays, or NULL              (arg 12)
+ *  stream  cudaStream_t                                               (arg 13)
+ */
+int arrow_eig(int n, const double *d, const double *z, double alpha,
+              double *lambda, double *V, int ldv, double *shift, double *mu,
+              const ae_opts *opts, ae_info *info, const ae_diag *diag, void *stream);
+
+/*
+ * arrow_eig_host -- arrow_eig on HOST buffers: copies d and z to the device,
+ * solves, and copies lambda (and V, shift, mu when non-NULL) back, all on
+ * `stream`, then synchronises.  Host buffers should be pinned for full
+ * copy bandwidth.  Arguments as arrow_eig; V is n x n with ldv = n.
+ */
+int arrow_eig_host(int n, const double *d_host, const double *z_host, double alpha,
+                   double *lambda_host, double *V_host, double *shift_host,
+                   double *mu_host, const ae_opts *opts, ae_info *info, void *stream);
+
+/*
+ * ae_debug_rcp -- the solver's FP64 reciprocal (Newton-Raphson refinement of
+ * the hardware approximation) applied to x[0..n) into y, for testing against
+ * IEEE division.  Device pointers.
+ */
+int ae_debug_rcp(int n, const double *x, double *y, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARROWHEAD_H */

@@ -1,0 +1,233 @@
+"""Thin ctypes binding of libarrowhead.so (include/arrowhead.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+PyTorch supplies device memory and the stream.  There is no CPU fallback: if
+the library has not been built, or no GPU is present, calls raise.
+
+Low-level symbols carry the C names (``lib().arrow_eig`` ...); the wrappers
+below with the same names take torch tensors and return torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libarrowhead.so")
+
+AE_OK = 0
+AE_ERR_CUDA = 1001
+AE_ERR_INPUT = 1002
+AE_ERR_NOCONV = 1003
+AE_FP64 = 0
+AE_FP32_BRACKET = 1
+FLAG_DEFLATED, FLAG_NEARZERO, FLAG_OTHERPOLE, FLAG_DPR1SHIFT = 1, 2, 4, 8
+FLAG_CAPPED, FLAG_SINGULAR, FLAG_FP32_FALLBACK = 16, 32, 64
+
+# every symbol include/arrowhead.h declares
+EXPORTED = ["ae_default_opts", "ae_status_string", "ae_last_cuda_error", "arrow_eig",
+            "arrow_eig_host", "ae_debug_rcp"]
+
+
+class AeOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("knu_max", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("fixup", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class AeInfo(ctypes.Structure):
+    _fields_ = [("n_reduced", ctypes.c_int), ("n_deflated", ctypes.c_int),
+                ("n_nearzero", ctypes.c_int), ("n_otherpole", ctypes.c_int),
+                ("n_dpr1shift", ctypes.c_int), ("n_capped", ctypes.c_int),
+                ("n_fp32_fallback", ctypes.c_int), ("max_iter_used", ctypes.c_int),
+                ("total_iter", ctypes.c_longlong), ("fix_iter", ctypes.c_longlong),
+                ("max_Kb", ctypes.c_double),
+                ("max_Knu", ctypes.c_double), ("ms_reduce", ctypes.c_float),
+                ("ms_eig", ctypes.c_float), ("ms_fix", ctypes.c_float),
+                ("ms_vectors", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AeDiag(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_void_p), ("Kb", ctypes.c_void_p), ("Knu", ctypes.c_void_p),
+                ("iters", ctypes.c_void_p), ("flags", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libarrowhead.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                "(the solver has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.ae_default_opts.argtypes = [ctypes.POINTER(AeOpts)]
+        L.ae_default_opts.restype = None
+        L.ae_status_string.argtypes = [I]
+        L.ae_status_string.restype = ctypes.c_char_p
+        L.ae_last_cuda_error.argtypes = []
+        L.ae_last_cuda_error.restype = ctypes.c_char_p
+        L.arrow_eig.argtypes = [I, P, P, D, P, P, I, P, P, ctypes.POINTER(AeOpts),
+                                ctypes.POINTER(AeInfo), ctypes.POINTER(AeDiag), P]
+        L.arrow_eig.restype = I
+        L.arrow_eig_host.argtypes = [I, P, P, D, P, P, P, P, ctypes.POINTER(AeOpts),
+                                     ctypes.POINTER(AeInfo), P]
+        L.arrow_eig_host.restype = I
+        L.ae_debug_rcp.argtypes = [I, P, P, P]
+        L.ae_debug_rcp.restype = I
+        _lib = L
+        return L
+
+
+class AeError(RuntimeError):
+    def __init__(self, fn, status):
+        L = lib()
+        msg = L.ae_status_string(status).decode()
+        if status == AE_ERR_CUDA:
+            msg += ": " + L.ae_last_cuda_error().decode()
+        super().__init__(f"{fn} returned {status} ({msg})")
+        self.status = status
+
+
+def default_opts(**kw) -> AeOpts:
+    o = AeOpts()
+    lib().ae_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check(fn, status):
+    if status != AE_OK:
+        raise AeError(fn, status)
+
+
+def arrow_eig(d, z, alpha, *, vectors=True, want_shift=False, opts=None, info=False,
+              diag=False, stream=None, out=None):
+    """Eigen-decomposition of [diag(d) z; z^T alpha] on the GPU.
+
+    ``d``, ``z``: float64 CUDA tensors of length n-1.  Returns a dict with
+    ``lam`` (n, descending), ``V`` (n x n column-major: column k is
+    ``V[:, k]`` of the returned (n, n) tensor) when ``vectors``, ``shift`` and
+    ``mu`` when ``want_shift``, ``info`` (dict, synchronises) and per-eigenpair
+    ``diag`` tensors when requested.  ``out`` may supply preallocated
+    ``lam``/``V`` tensors.
+    """
+    import torch
+    dev = d.device
+    n = int(d.numel()) + 1
+    out = dict(out or {})
+    lam = out.get("lam")
+    if lam is None:
+        lam = torch.empty(n, dtype=torch.float64, device=dev)
+    V = out.get("V") if vectors else None
+    if vectors and V is None:
+        # storage is column-major n x n: allocate (n, n) row-major and view transposed
+        V = torch.empty((n, n), dtype=torch.float64, device=dev)
+    shift = torch.empty(n, dtype=torch.float64, device=dev) if want_shift else None
+    mu = torch.empty(n, dtype=torch.float64, device=dev) if want_shift else None
+    o = opts if opts is not None else default_opts()
+    inf = AeInfo() if info else None
+    dg = None
+    dgt = {}
+    if diag:
+        dgt = {"b": torch.empty(n, dtype=torch.float64, device=dev),
+               "Kb": torch.empty(n, dtype=torch.float64, device=dev),
+               "Knu": torch.empty(n, dtype=torch.float64, device=dev),
+               "iters": torch.empty(n, dtype=torch.int32, device=dev),
+               "flags": torch.empty(n, dtype=torch.int32, device=dev)}
+        dg = AeDiag(*(t.data_ptr() for t in dgt.values()))
+    st = lib().arrow_eig(n, _ptr(d), _ptr(z), float(alpha), _ptr(lam), _ptr(V), n,
+                         _ptr(shift), _ptr(mu), ctypes.byref(o),
+                         ctypes.byref(inf) if inf is not None else None,
+                         ctypes.byref(dg) if dg is not None else None,
+                         _stream_handle(stream))
+    _check("arrow_eig", st)
+    res = {"lam": lam}
+    if vectors:
+        res["V"] = V.t()          # column k of the column-major matrix
+    if want_shift:
+        res["shift"], res["mu"] = shift, mu
+    if info:
+        res["info"] = inf.as_dict()
+    if diag:
+        res["diag"] = dgt
+    return res
+
+
+def arrow_eig_host(d, z, alpha, *, vectors=True, want_shift=False, opts=None, stream=None,
+                   out=None):
+    """arrow_eig on host arrays (numpy or pinned torch CPU tensors).
+
+    The library copies the inputs to the device, solves and copies the results
+    back on ``stream`` and synchronises.  ``out`` may supply pinned host
+    ``lam``/``V`` buffers (torch CPU tensors)."""
+    import torch
+    d = torch.as_tensor(d, dtype=torch.float64)
+    z = torch.as_tensor(z, dtype=torch.float64)
+    n = int(d.numel()) + 1
+    out = dict(out or {})
+    lam = out.get("lam")
+    if lam is None:
+        lam = torch.empty(n, dtype=torch.float64)
+    V = out.get("V") if vectors else None
+    if vectors and V is None:
+        V = torch.empty((n, n), dtype=torch.float64)
+    shift = torch.empty(n, dtype=torch.float64) if want_shift else None
+    mu = torch.empty(n, dtype=torch.float64) if want_shift else None
+    o = opts if opts is not None else default_opts()
+    st = lib().arrow_eig_host(n, _ptr(d.contiguous()), _ptr(z.contiguous()), float(alpha),
+                              _ptr(lam), _ptr(V), _ptr(shift), _ptr(mu), ctypes.byref(o), None,
+                              _stream_handle(stream))
+    _check("arrow_eig_host", st)
+    res = {"lam": lam}
+    if vectors:
+        res["V"] = V.t()
+    if want_shift:
+        res["shift"], res["mu"] = shift, mu
+    return res
+
+
+def debug_rcp(x, stream=None):
+    """The solver's FP64 reciprocal applied elementwise (device tensor)."""
+    import torch
+    y = torch.empty_like(x)
+    _check("ae_debug_rcp", lib().ae_debug_rcp(int(x.numel()), _ptr(x), _ptr(y),
+                                              _stream_handle(stream)))
+    return y
+
+
+def exported_symbols(path=LIB_PATH):
+    """Names of the C-ABI symbols present in the library (no GPU needed)."""
+    L = ctypes.CDLL(path)
+    return [s for s in EXPORTED if hasattr(L, s)]
+
+
+__all__ = ["arrow_eig", "arrow_eig_host", "debug_rcp", "default_opts", "lib", "AeOpts",
+           "AeInfo", "AeDiag", "AeError", "exported_symbols", "EXPORTED"]
+
+_ = np  # numpy is used by callers passing host arrays

@@ -1,0 +1,235 @@
+// ae_api.cu -- the extern "C" entry points declared in include/arrowhead.h.
+// Argument checking, option defaults, scratch allocation (stream-ordered) and
+// the optional synchronising summary; all arithmetic is in the kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "ae_internal.h"
+
+namespace {
+
+thread_local char g_err[256] = "";
+
+int cuda_fail(cudaError_t e) {
+    snprintf(g_err, sizeof(g_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return AE_ERR_CUDA;
+}
+
+// keep freed stream-ordered allocations in the device's pool so repeated
+// calls do not return memory to the driver at every synchronisation
+void keep_pool_warm() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    static int done_mask = 0;
+    if (dev < 31 && (done_mask & (1 << dev))) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (dev < 31) done_mask |= 1 << dev;
+}
+
+int resolve_opts(const ae_opts *o, ae::RunOpts &ro) {
+    ae_opts def;
+    ae_default_opts(&def);
+    if (!o) o = &def;
+    if (o->precision != AE_FP64 && o->precision != AE_FP32_BRACKET) return 1;
+    ro.precision = o->precision;
+    ro.knu_max = o->knu_max > 0.0 ? o->knu_max : def.knu_max;
+    ro.max_iter = o->max_iter > 0 ? o->max_iter : def.max_iter;
+    ro.fixup = o->fixup ? 1 : 0;
+    for (int i = 0; i < 5; ++i) ro.ev[i] = nullptr;
+    return 0;
+}
+
+// events for opts->profile; destroyed after the synchronising summary
+struct Prof {
+    bool on = false;
+    cudaEvent_t ev[5] = {};
+    ~Prof() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    cudaError_t init(ae::RunOpts &ro) {
+        on = true;
+        for (int i = 0; i < 5; ++i) {
+            cudaError_t e = cudaEventCreate(&ev[i]);
+            if (e != cudaSuccess) return e;
+            ro.ev[i] = ev[i];
+        }
+        return cudaSuccess;
+    }
+};
+
+double bits_to_double(unsigned long long u) {
+    double v;
+    memcpy(&v, &u, sizeof(v));
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ae_default_opts(ae_opts *opts) {
+    if (!opts) return;
+    opts->precision = AE_FP64;
+    opts->knu_max = 10.0;
+    opts->max_iter = 2200;
+    opts->fixup = 1;
+    opts->profile = 0;
+}
+
+const char *ae_status_string(int status) {
+    if (status == AE_OK) return "ok";
+    if (status < 0) return "invalid argument";
+    switch (status) {
+        case AE_ERR_CUDA: return "CUDA error";
+        case AE_ERR_INPUT: return "non-finite input";
+        case AE_ERR_NOCONV: return "iteration cap reached";
+        default: return "unknown status";
+    }
+}
+
+const char *ae_last_cuda_error(void) { return g_err; }
+
+int arrow_eig(int n, const double *d, const double *z, double alpha, double *lambda,
+              double *V, int ldv, double *shift, double *mu, const ae_opts *opts,
+              ae_info *info, const ae_diag *diag, void *stream) {
+    if (n < 1) return -1;
+    if (n > 1 && !d) return -2;
+    if (n > 1 && !z) return -3;
+    if (!isfinite(alpha)) return -4;
+    if (!lambda) return -5;
+    if (V && ldv < n) return -7;
+    ae::RunOpts ro;
+    if (resolve_opts(opts, ro)) return -10;
+    cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_warm();
+    Prof prof;
+    if (opts && opts->profile && info) {
+        cudaError_t pe = prof.init(ro);
+        if (pe != cudaSuccess) return cuda_fail(pe);
+    }
+    void *base = nullptr;
+    cudaError_t e = cudaMallocAsync(&base, ae::arrow_scratch_bytes(n), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ae::Scratch S = ae::carve_scratch(base, n);
+    ae::Outputs out;
+    out.lambda = lambda;
+    out.V = V;
+    out.ldv = ldv;
+    out.shift = shift;
+    out.mu = mu;
+    out.dg_b = diag ? diag->b : nullptr;
+    out.dg_Kb = diag ? diag->Kb : nullptr;
+    out.dg_Knu = diag ? diag->Knu : nullptr;
+    out.dg_iters = diag ? diag->iters : nullptr;
+    out.dg_flags = diag ? diag->flags : nullptr;
+    int status = AE_OK;
+    e = ae::launch_arrow(n, d, z, alpha, out, ro, S, st);
+    if (e != cudaSuccess) status = cuda_fail(e);
+    if (info && status == AE_OK) {
+        int cnt[ae::C_COUNT];
+        unsigned long long c64[ae::C64_COUNT];
+        e = cudaMemcpyAsync(cnt, S.cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c64, S.cnt64, sizeof(c64), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            status = cuda_fail(e);
+        } else {
+            memset(info, 0, sizeof(*info));
+            info->n_reduced = cnt[ae::C_M] + 1;
+            info->n_deflated = cnt[ae::C_ND];
+            info->n_nearzero = cnt[ae::C_NEARZERO];
+            info->n_otherpole = cnt[ae::C_OTHERPOLE];
+            info->n_dpr1shift = cnt[ae::C_DPR1];
+            info->n_capped = cnt[ae::C_CAPPED];
+            info->n_fp32_fallback = cnt[ae::C_FP32FB];
+            info->max_iter_used = cnt[ae::C_MAXIT];
+            info->total_iter = (long long)c64[ae::C64_ITERS];
+            info->fix_iter = (long long)c64[ae::C64_ITERS_FIX];
+            info->max_Kb = bits_to_double(c64[ae::C64_MAXKB]);
+            info->max_Knu = bits_to_double(c64[ae::C64_MAXKNU]);
+            if (prof.on) {
+                cudaEventElapsedTime(&info->ms_reduce, prof.ev[0], prof.ev[1]);
+                cudaEventElapsedTime(&info->ms_eig, prof.ev[1], prof.ev[2]);
+                cudaEventElapsedTime(&info->ms_fix, prof.ev[2], prof.ev[3]);
+                cudaEventElapsedTime(&info->ms_vectors, prof.ev[3], prof.ev[4]);
+            }
+            if (cnt[ae::C_FLAGS] & ae::CF_BAD) status = AE_ERR_INPUT;
+            else if (cnt[ae::C_CAPPED]) status = AE_ERR_NOCONV;
+        }
+    }
+    e = cudaFreeAsync(base, st);
+    if (e != cudaSuccess && status == AE_OK) status = cuda_fail(e);
+    return status;
+}
+
+int arrow_eig_host(int n, const double *d_host, const double *z_host, double alpha,
+                   double *lambda_host, double *V_host, double *shift_host, double *mu_host,
+                   const ae_opts *opts, ae_info *info, void *stream) {
+    if (n < 1) return -1;
+    if (n > 1 && !d_host) return -2;
+    if (n > 1 && !z_host) return -3;
+    if (!isfinite(alpha)) return -4;
+    if (!lambda_host) return -5;
+    cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_warm();
+    const size_t n1 = (size_t)(n - 1);
+    const size_t vbytes = V_host ? sizeof(double) * (size_t)n * (size_t)n : 0;
+    const size_t bytes = 256 * 6 + sizeof(double) * (2 * n1 + 3 * (size_t)n) + vbytes;
+    void *base = nullptr;
+    cudaError_t e = cudaMallocAsync(&base, bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    char *p = (char *)base;
+    auto take = [&](size_t b) {
+        char *q = p;
+        p += (b + 255) & ~(size_t)255;
+        return (double *)q;
+    };
+    double *dd_ = take(sizeof(double) * (n1 ? n1 : 1));
+    double *dz = take(sizeof(double) * (n1 ? n1 : 1));
+    double *dl = take(sizeof(double) * n);
+    double *ds = shift_host ? take(sizeof(double) * n) : nullptr;
+    double *dm = mu_host ? take(sizeof(double) * n) : nullptr;
+    double *dV = V_host ? take(vbytes) : nullptr;
+    int status = AE_OK;
+    if (n1) {
+        e = cudaMemcpyAsync(dd_, d_host, sizeof(double) * n1, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dz, z_host, sizeof(double) * n1, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) status = cuda_fail(e);
+    }
+    if (status == AE_OK)
+        status = arrow_eig(n, dd_, dz, alpha, dl, dV, n, ds, dm, opts, info, nullptr, stream);
+    if (status == AE_OK) {
+        e = cudaMemcpyAsync(lambda_host, dl, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && dV)
+            e = cudaMemcpyAsync(V_host, dV, vbytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && ds)
+            e = cudaMemcpyAsync(shift_host, ds, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && dm)
+            e = cudaMemcpyAsync(mu_host, dm, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) status = cuda_fail(e);
+    }
+    cudaError_t e2 = cudaFreeAsync(base, st);
+    cudaError_t e3 = cudaStreamSynchronize(st);
+    if (status == AE_OK && e2 != cudaSuccess) status = cuda_fail(e2);
+    if (status == AE_OK && e3 != cudaSuccess) status = cuda_fail(e3);
+    return status;
+}
+
+int ae_debug_rcp(int n, const double *x, double *y, void *stream) {
+    if (n < 0) return -1;
+    if (n > 0 && !x) return -2;
+    if (n > 0 && !y) return -3;
+    cudaError_t e = ae::launch_debug_rcp(n, x, y, (cudaStream_t)stream);
+    return e == cudaSuccess ? AE_OK : cuda_fail(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// ae_internal.h -- types shared by the library's translation units (not part
+// of the public C ABI, which is include/arrowhead.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "arrowhead.h"
+
+namespace ae {
+
+// slots of the int counter block
+enum {
+    C_M = 0,          // number of reduced poles m
+    C_ND = 1,         // number of deflated rows
+    C_FLAGS = 2,      // CF_* bits from k_check
+    C_WORK = 3,       // work ticket of k_eig
+    C_NFIX = 4,       // length of the remedy list
+    C_WORK2 = 5,      // work ticket of k_fix_solve
+    C_NEARZERO = 6,
+    C_OTHERPOLE = 7,
+    C_DPR1 = 8,
+    C_CAPPED = 9,
+    C_MAXIT = 10,
+    C_FP32FB = 11,
+    C_COUNT = 16
+};
+enum { C64_ITERS = 0, C64_MAXKB = 1, C64_MAXKNU = 2, C64_ITERS_FIX = 3, C64_COUNT = 4 };
+
+// k_check flag bits
+enum { CF_UNSORTED = 1, CF_ZERO = 2, CF_BAD = 4, CF_ZEROPOLE = 8 };
+
+struct Scratch {
+    int *cnt;
+    unsigned long long *cnt64;
+    int *perm;      // sorted position -> input row
+    int *spos;      // input row -> sorted position
+    int *kind;      // input row: 0 pole head, 1 zero spike, 2 folded into a run
+    int *run_s0;    // folded row: sorted position where its run starts
+    double *run_R;  // folded row: R_{m-1}, R_m
+    double *pd, *pz, *pz2;  // reduced poles / spikes / fl(spike^2)
+    int *prow;      // reduced pole -> input row of its head
+    int *drow;      // deflated rows in sorted order
+    double *dval;   // their pole values
+    double *es_sigma, *es_mu, *es_lam, *es_b, *es_Kb, *es_Knu, *es_fixshift;
+    int *es_pole, *es_iters, *es_flags, *es_fixpole, *fixlist;
+    int *pos;       // output position of computed (first m+1) and deflated items
+};
+
+struct Outputs {
+    double *lambda;
+    double *V;
+    long long ldv;
+    double *shift, *mu;
+    double *dg_b, *dg_Kb, *dg_Knu;
+    int *dg_iters, *dg_flags;
+};
+
+struct RunOpts {
+    int precision;
+    double knu_max;
+    int max_iter;
+    int fixup;
+    cudaEvent_t ev[5];   // phase boundaries when profiling (else null)
+};
+
+size_t arrow_scratch_bytes(int n);
+Scratch carve_scratch(void *base, int n);
+cudaError_t launch_arrow(int n, const double *d, const double *z, double alpha,
+                         const Outputs &out, const RunOpts &ro, Scratch S, cudaStream_t st);
+cudaError_t launch_debug_rcp(int n, const double *x, double *y, cudaStream_t st);
+
+}  // namespace ae

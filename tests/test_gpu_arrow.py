@@ -1,0 +1,206 @@
+"""GPU parity of arrow_eig (through the C ABI) against the CPU oracle.
+
+Every eigenvalue and eigenvector component within 10 n eps64 of the oracle;
+reduction decisions and output order exact.  Sizes span several 32-lane
+strides with ragged tails; the full-size graded n = 16384 case runs in the
+same configuration the benchmark times and is checked on sampled columns the
+oracle computes one by one, plus properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import read_golden
+from parity import assert_parity, tolerance
+from paper_1302_7203_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ae():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1302_7203_gb300 import arrowhead, build
+    build.build()
+    return arrowhead
+
+
+def gpu_solve(ae, d, z, alpha, **kw):
+    dt = torch.as_tensor(np.asarray(d, dtype=np.float64), device="cuda")
+    zt = torch.as_tensor(np.asarray(z, dtype=np.float64), device="cuda")
+    r = ae.arrow_eig(dt, zt, alpha, **kw)
+    torch.cuda.synchronize()
+    out = {"lam": r["lam"].cpu().numpy()}
+    if "V" in r:
+        out["V"] = r["V"].cpu().numpy()
+    for k in ("shift", "mu"):
+        if k in r:
+            out[k] = r[k].cpu().numpy()
+    if "info" in r:
+        out["info"] = r["info"]
+    if "diag" in r:
+        out["diag"] = {k: v.cpu().numpy() for k, v in r["diag"].items()}
+    return out
+
+
+def check_full(ae, d, z, alpha, what, factor=10.0, **kw):
+    n = len(d) + 1
+    g = gpu_solve(ae, d, z, alpha, info=True, **kw)
+    o = oracle.arrow_eig(d, z, alpha)
+    assert_parity(g["lam"], g["V"], o, n, factor=factor, what=what)
+    return g, o
+
+
+# ---------------------------------------------------------------------------
+def test_reciprocal_is_faithful(ae):
+    rng = np.random.default_rng(0)
+    x = rng.uniform(1, 2, 200000) * np.exp2(rng.integers(-1000, 1000, 200000))
+    x *= np.where(rng.random(x.size) < 0.5, -1, 1)
+    xt = torch.as_tensor(x, device="cuda")
+    y = ae.debug_rcp(xt).cpu().numpy()
+    ref = (1.0 / xt).cpu().numpy()          # IEEE division on the GPU
+    ulps = np.abs(y - ref) / np.spacing(np.abs(ref))
+    assert ulps.max() <= 1.0
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_paper_examples(ae, k):
+    d, z, a = W.paper_example(k)
+    g, o = check_full(ae, d, z, a, f"Example {k}", want_shift=True, diag=True)
+    assert np.all(g["V"][-1] < 0)
+
+
+def test_example3_doubled_precision_element(ae):
+    d, z, a = W.paper_example(3)
+    g = gpu_solve(ae, d, z, a, want_shift=True, diag=True)
+    rows = read_golden("example3.txt")
+    b_doubled = [float(v[0]) for key, v in rows if key == "b_doubled"][0]
+    # eigenvalue 2 (index 1) is computed with the shift d_2 = 4 (A_2 of Example 3)
+    assert g["shift"][1] == 4.0
+    assert abs(g["diag"]["b"][1] - b_doubled) <= 2 * np.spacing(b_doubled)
+    # K_b of Eq. (K2) for shifts d_2..d_5 (printed to ~7 meaningful digits)
+    kb_ref = [float(v[2]) for key, v in rows if key == "knu_kb"]
+    np.testing.assert_allclose(g["diag"]["Kb"][1:6], kb_ref, rtol=3e-7)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 31, 32, 33, 34, 63, 64, 65, 97, 300])
+def test_uniform_sizes(ae, n):
+    d, z, a = W.uniform_arrow(n, seed=n)
+    check_full(ae, d, z, a, f"uniform n={n}")
+
+
+def test_uniform_n1000_full(ae):
+    d, z, a = W.uniform_arrow(1000, seed=0)
+    g, _ = check_full(ae, d, z, a, "uniform n=1000 (seed 0)")
+    assert g["info"]["n_reduced"] == 1000 and g["info"]["n_deflated"] == 0
+
+
+@pytest.mark.parametrize("n,seed", [(200, 11), (1000, 12), (3001, 13)])
+def test_graded(ae, n, seed):
+    d, z, a = W.graded_arrow(n, seed=seed)
+    check_full(ae, d, z, a, f"graded n={n}")
+
+
+def test_quantum_dot_like(ae):
+    d, z, a = W.quantum_dot_like(2501)
+    check_full(ae, d, z, a, "quantum-dot-like n=2501")
+
+
+def test_order_one_and_two(ae):
+    g = gpu_solve(ae, np.zeros(0), np.zeros(0), 2.5)
+    assert g["lam"][0] == 2.5 and g["V"][0, 0] == -1.0
+    check_full(ae, [1.0], [0.5], -0.25, "n=2")
+
+
+def test_mirrored_exact_zero(ae):
+    d, z, a = W.mirrored_arrow(41)
+    g, o = check_full(ae, d, z, a, "mirrored", want_shift=True)
+    lam = g["lam"]
+    assert abs(lam[20]) <= 1e-25 * np.abs(lam).max()
+
+
+def test_deflation_and_ordering(ae):
+    # unsorted, negative spikes, zero spikes (+0, -0), runs of equal poles
+    d = np.array([0.5, 3.0, 2.0, 3.0, -1.0, 3.0, 2.0, 7.5, -1.0, 0.25])
+    z = np.array([0.5, -1.0, 0.0, 2.0, 1.0, -0.0, 0.25, -3.0, 0.125, 1.5])
+    g, o = check_full(ae, d, z, 0.3, "deflation", want_shift=True, diag=True)
+    assert g["info"]["n_deflated"] == 4
+    # the deflated zero-spike rows return their unit vectors exactly
+    for row in (2, 5):
+        k = np.nonzero(np.all(g["V"] == np.eye(11)[:, [row]], axis=0))[0]
+        assert k.size == 1 and g["lam"][k[0]] == d[row]
+
+
+def test_all_deflated(ae):
+    d = np.array([1.0, -2.0, 3.0])
+    z = np.zeros(3)
+    check_full(ae, d, z, 0.5, "all zero spikes")
+
+
+def test_shuffle_scale_and_sign_invariance(ae):
+    d, z, a = W.graded_arrow(700, seed=21)
+    g0 = gpu_solve(ae, d, z, a)
+    perm = np.random.default_rng(1).permutation(len(d))
+    g1 = gpu_solve(ae, d[perm], z[perm], a)
+    np.testing.assert_array_equal(g1["lam"], g0["lam"])
+    np.testing.assert_array_equal(g1["V"][:-1], g0["V"][:-1][perm])
+    g2 = gpu_solve(ae, d * 2.0 ** 40, z * 2.0 ** 40, a * 2.0 ** 40)
+    np.testing.assert_array_equal(g2["lam"], g0["lam"] * 2.0 ** 40)
+    np.testing.assert_array_equal(g2["V"], g0["V"])
+    zs = z.copy()
+    zs[[0, 5, 99]] *= -1
+    g3 = gpu_solve(ae, d, zs, a)
+    V = g0["V"].copy()
+    V[[0, 5, 99]] *= -1
+    np.testing.assert_array_equal(g3["lam"], g0["lam"])
+    np.testing.assert_array_equal(g3["V"], V)
+
+
+def test_deterministic(ae):
+    d, z, a = W.uniform_arrow(2000, seed=3)
+    g0 = gpu_solve(ae, d, z, a)
+    g1 = gpu_solve(ae, d, z, a)
+    np.testing.assert_array_equal(g0["lam"], g1["lam"])
+    np.testing.assert_array_equal(g0["V"], g1["V"])
+
+
+def test_host_entry_point_matches_device(ae):
+    d, z, a = W.uniform_arrow(500, seed=5)
+    g = gpu_solve(ae, d, z, a)
+    h = ae.arrow_eig_host(d, z, a)
+    np.testing.assert_array_equal(h["lam"].numpy(), g["lam"])
+    np.testing.assert_array_equal(h["V"].numpy(), g["V"])
+
+
+def test_invalid_input_reported(ae):
+    d = np.array([1.0, np.nan, 0.5])
+    z = np.ones(3)
+    with pytest.raises(ae.AeError) as ei:
+        gpu_solve(ae, d, z, 0.0, info=True)
+    assert ei.value.status == ae.AE_ERR_INPUT
+
+
+def test_graded_full_size_sampled(ae):
+    """n = 16384 graded (the benchmark workload): sampled parity + properties."""
+    n = 16384
+    d, z, a = W.graded_arrow(n, seed=1)
+    g = gpu_solve(ae, d, z, a, info=True, want_shift=True, diag=True)
+    lam, V = g["lam"], g["V"]
+    # properties at full size: interlacing, unit columns, x_n = -1 sign
+    assert np.all(lam[:-1] >= d) and np.all(d >= lam[1:])
+    np.testing.assert_allclose(np.linalg.norm(V, axis=0), 1.0, atol=4 * n * 2.0 ** -53)
+    assert np.all(V[-1] < 0)
+    # sampled columns: ends, a spread, and every column a remedy touched
+    flags = g["diag"]["flags"]
+    fixed = np.nonzero(flags & (ae.FLAG_NEARZERO | ae.FLAG_OTHERPOLE | ae.FLAG_DPR1SHIFT))[0]
+    rng = np.random.default_rng(7)
+    ks = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1],
+                                   rng.choice(n, 96, replace=False), fixed[:64]]))
+    o = oracle.arrow_eig(d, z, a, ks=ks)
+    assert_parity(lam[ks], V[:, ks], o, n, cols=ks, what="graded n=16384 sampled")
+    # orthogonality of the sampled columns
+    G = V[:, ks].T @ V[:, ks] - np.eye(ks.size)
+    assert np.abs(G).max() <= 10 * n * 2.0 ** -53
