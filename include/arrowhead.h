@@ -91,8 +91,9 @@ typedef struct ae_info {
 /* Optional per-eigenpair diagnostics (device arrays of length n, any may be
    NULL), indexed like the returned eigenvalues. */
 typedef struct ae_diag {
-    double *b;       /* element b of Eq. (b_ob) used by the final solve (NaN if none) */
-    double *Kb;      /* K_b of Eq. (K2) for the shift pole */
+    double *b;       /* element b of Eq. (b_ob) for Algorithm 1's shift pole (NaN if none),
+                        also when a remedy recomputed the eigenvalue */
+    double *Kb;      /* K_b of Eq. (K2) for that shift pole */
     double *Knu;     /* K_nu of Eq. (K0) estimated from the neighbouring eigenvalues */
     int *iters;      /* FP64 bisection steps of the final solve */
     int *flags;      /* AE_FLAG_* bits */

@@ -314,6 +314,9 @@ __global__ void __launch_bounds__(256) k_fix_solve(double alpha, Scratch S, Solv
         const bool ok = (res.lam >= lo && res.lam <= hi) && isfinite(res.lam);
         if (lane == 0) {
             if (ok) {
+                // b and K_b stay those of Algorithm 1's shift pole
+                res.b = S.es_b[k];
+                res.Kb = S.es_Kb[k];
                 store_result(S, k, res);
                 S.es_flags[k] = f | res.flags;
                 record_stats(S, res, true);
