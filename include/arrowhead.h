@@ -45,6 +45,7 @@ extern "C" {
 #define AE_ERR_CUDA 1001      /* a CUDA runtime call failed (see ae_last_cuda_error) */
 #define AE_ERR_INPUT 1002     /* device-side check: non-finite d, z or alpha */
 #define AE_ERR_NOCONV 1003    /* some eigenpair reached opts->max_iter */
+#define AE_ERR_TOO_LARGE 1004 /* arrow_eig_noalloc: n exceeds its static scratch */
 
 /* precision of the bisection (see ae_opts.precision) */
 #define AE_FP64 0             /* all-FP64 bisection from the Gershgorin bracket */
@@ -152,6 +153,32 @@ int arrow_eig(int n, const double *d, const double *z, double alpha,
 int arrow_eig_host(int n, const double *d_host, const double *z_host, double alpha,
                    double *lambda_host, double *V_host, double *shift_host,
                    double *mu_host, const ae_opts *opts, ae_info *info, void *stream);
+
+/*
+ * arrow_eig_noalloc -- arrow_eig that allocates nothing.  The paper has no
+ * counterpart: this is an interface for callers that cannot allocate device
+ * memory while they run, e.g. an application that reserves all GPU memory up
+ * front and hands the library only its input and output buffers, or a
+ * latency-critical loop where an allocation could block, fail under memory
+ * pressure or fragment a reserved pool.
+ *
+ * Arguments, outputs and return codes are those of arrow_eig (opts->profile is
+ * ignored).  The solve's scratch lives in one static device array of
+ * AE_NOALLOC_SCRATCH_BYTES (4 MiB) that every GPU loading the library holds
+ * until the process exits; n is limited to what fits, n <= 27585 (larger n
+ * returns AE_ERR_TOO_LARGE without touching the GPU).  The call issues no
+ * cudaMalloc/cudaFree and no allocating library routine.
+ *  - Its first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the one array: calls that may overlap on the
+ *    GPU (different streams, or different host threads) race and corrupt each
+ *    other's results.  Serialise them, e.g. on one stream.
+ */
+#define AE_NOALLOC_SCRATCH_BYTES (4u << 20)
+int arrow_eig_noalloc(int n, const double *d, const double *z, double alpha,
+                      double *lambda, double *V, int ldv, double *shift, double *mu,
+                      const ae_opts *opts, ae_info *info, const ae_diag *diag, void *stream);
 
 /*
  * ae_debug_rcp -- the solver's FP64 reciprocal (Newton-Raphson refinement of

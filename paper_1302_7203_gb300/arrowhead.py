@@ -29,7 +29,8 @@ FLAG_CAPPED, FLAG_SINGULAR, FLAG_FP32_FALLBACK = 16, 32, 64
 
 # every symbol include/arrowhead.h declares
 EXPORTED = ["ae_default_opts", "ae_status_string", "ae_last_cuda_error", "arrow_eig",
-            "arrow_eig_host", "ae_debug_rcp"]
+            "arrow_eig_host", "arrow_eig_noalloc", "ae_debug_rcp"]
+AE_ERR_TOO_LARGE = 1004
 
 
 class AeOpts(ctypes.Structure):
@@ -86,6 +87,8 @@ def lib():
         L.arrow_eig_host.argtypes = [I, P, P, D, P, P, P, P, ctypes.POINTER(AeOpts),
                                      ctypes.POINTER(AeInfo), P]
         L.arrow_eig_host.restype = I
+        L.arrow_eig_noalloc.argtypes = L.arrow_eig.argtypes
+        L.arrow_eig_noalloc.restype = I
         L.ae_debug_rcp.argtypes = [I, P, P, P]
         L.ae_debug_rcp.restype = I
         _lib = L

@@ -72,6 +72,10 @@ double bits_to_double(unsigned long long u) {
 
 }  // namespace
 
+namespace ae {
+void record_cuda_error(cudaError_t e) { cuda_fail(e); }
+}  // namespace ae
+
 extern "C" {
 
 void ae_default_opts(ae_opts *opts) {
@@ -90,6 +94,9 @@ const char *ae_status_string(int status) {
         case AE_ERR_CUDA: return "CUDA error";
         case AE_ERR_INPUT: return "non-finite input";
         case AE_ERR_NOCONV: return "iteration cap reached";
+        case AE_ERR_TOO_LARGE:
+            return "n too large for the static scratch of arrow_eig_noalloc "
+                   "(AE_NOALLOC_SCRATCH_BYTES)";
         default: return "unknown status";
     }
 }

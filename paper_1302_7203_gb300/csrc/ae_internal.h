@@ -68,5 +68,7 @@ Scratch carve_scratch(void *base, int n);
 cudaError_t launch_arrow(int n, const double *d, const double *z, double alpha,
                          const Outputs &out, const RunOpts &ro, Scratch S, cudaStream_t st);
 cudaError_t launch_debug_rcp(int n, const double *x, double *y, cudaStream_t st);
+// remember a CUDA error for ae_last_cuda_error()
+void record_cuda_error(cudaError_t e);
 
 }  // namespace ae
