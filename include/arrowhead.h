@@ -165,7 +165,7 @@ int arrow_eig_host(int n, const double *d_host, const double *z_host, double alp
  * Arguments, outputs and return codes are those of arrow_eig (opts->profile is
  * ignored).  The solve's scratch lives in one static device array of
  * AE_NOALLOC_SCRATCH_BYTES (4 MiB) that every GPU loading the library holds
- * until the process exits; n is limited to what fits, n <= 27585 (larger n
+ * until the process exits; n is limited to what fits, n <= 25537 (larger n
  * returns AE_ERR_TOO_LARGE without touching the GPU).  The call issues no
  * cudaMalloc/cudaFree and no allocating library routine.
  *  - Its first call on a device looks up the array's device address

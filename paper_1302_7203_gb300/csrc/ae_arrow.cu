@@ -173,6 +173,42 @@ __global__ void __launch_bounds__(1024) k_reduce(int n1, const double *__restric
         S.cnt[C_M] = carry_keep;
         S.cnt[C_ND] = carry_defl;
     }
+    // FP32 copies for the opening bracket, scaled by powers of two so that the
+    // largest |pole| and the largest spike^2 are O(1)
+    __syncthreads();
+    __shared__ double red[2][32];
+    const int m = carry_keep;
+    double mxd = 0.0, mxz = 0.0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        mxd = fmax(mxd, fabs(S.pd[j]));
+        mxz = fmax(mxz, S.pz2[j]);
+    }
+    mxd = warp_max(mxd);
+    mxz = warp_max(mxz);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = mxd;
+        red[1][threadIdx.x >> 5] = mxz;
+    }
+    __syncthreads();
+    mxd = 0.0;
+    mxz = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        mxd = fmax(mxd, red[0][w]);
+        mxz = fmax(mxz, red[1][w]);
+    }
+    const double ds = (mxd > 0.0 && isfinite(mxd)) ? ldexp(1.0, -ilogb(mxd)) : 1.0;
+    const double zs = (mxz > 0.0 && isfinite(mxz)) ? ldexp(1.0, -ilogb(mxz)) : 1.0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const double v = S.pd[j] * ds;
+        const float h = (float)v;
+        S.pdh[j] = h;
+        S.pdl[j] = (float)(v - (double)h);
+        S.pz2f[j] = (float)(S.pz2[j] * zs);
+    }
+    if (threadIdx.x == 0) {
+        S.fscale[0] = ds;
+        S.fscale[1] = zs;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -194,6 +230,7 @@ __device__ __forceinline__ void record_stats(const Scratch &S, const EigResult &
     if (fix) atomicAdd(S.cnt64 + C64_ITERS_FIX, (unsigned long long)r.iters);
     atomicMax(S.cnt + C_MAXIT, r.iters);
     if (r.flags & AE_FLAG_CAPPED) atomicAdd(S.cnt + C_CAPPED, 1);
+    if (r.flags & AE_FLAG_FP32_FALLBACK) atomicAdd(S.cnt + C_FP32FB, 1);
     if (isfinite(r.Kb)) atomic_max_nonneg(S.cnt64 + C64_MAXKB, r.Kb);
 }
 
@@ -201,7 +238,8 @@ __global__ void __launch_bounds__(256) k_eig(double alpha, Scratch S, SolveOpts 
     const int lane = threadIdx.x & 31;
     const int m = S.cnt[C_M];
     const int ncomp = m + 1;
-    const ArrowPoles R = {m, S.pd, S.pz, S.pz2, alpha};
+    const ArrowPoles R = {m,       S.pd,   S.pz,   S.pz2,          alpha,
+                          S.pdh,   S.pdl,  S.pz2f, S.fscale[0],    S.fscale[1]};
     for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(S.cnt + C_WORK, 1);
@@ -290,7 +328,8 @@ __global__ void __launch_bounds__(256) k_fix_solve(double alpha, Scratch S, Solv
     const int lane = threadIdx.x & 31;
     const int m = S.cnt[C_M];
     const int nfix = S.cnt[C_NFIX];
-    const ArrowPoles R = {m, S.pd, S.pz, S.pz2, alpha};
+    const ArrowPoles R = {m,       S.pd,   S.pz,   S.pz2,          alpha,
+                          S.pdh,   S.pdl,  S.pz2f, S.fscale[0],    S.fscale[1]};
     for (;;) {
         int w = 0;
         if (lane == 0) w = atomicAdd(S.cnt + C_WORK2, 1);
@@ -474,64 +513,59 @@ static int sm_count() {
     return cached;
 }
 
-size_t arrow_scratch_bytes(int n) {
+// One layout routine serves both sizing and carving, so they cannot disagree:
+// every array starts on a 256-byte boundary.
+static size_t layout(uintptr_t base, int n, Scratch *S) {
     const size_t n1 = n > 1 ? (size_t)n - 1 : 1;
     const size_t nn = (size_t)n;
-    size_t b = 0;
-    auto add = [&](size_t bytes) { b += (bytes + 255) & ~(size_t)255; };
-    add(sizeof(int) * C_COUNT);
-    add(sizeof(unsigned long long) * C64_COUNT);
-    add(sizeof(int) * n1);       // perm
-    add(sizeof(int) * n1);       // spos
-    add(sizeof(int) * n1);       // kind
-    add(sizeof(int) * n1);       // run_s0
-    add(sizeof(double) * 2 * n1);  // run_R
-    add(sizeof(double) * n1 * 3);  // pd, pz, pz2
-    add(sizeof(int) * n1);       // prow
-    add(sizeof(int) * n1);       // drow
-    add(sizeof(double) * n1);    // dval
-    add(sizeof(double) * nn * 7);  // es_sigma, mu, lam, b, Kb, Knu, fixshift
-    add(sizeof(int) * nn * 5);   // es_pole, iters, flags, fixpole, fixlist
-    add(sizeof(int) * nn);       // pos
-    return b + 256;
-}
-
-Scratch carve_scratch(void *base, int n) {
-    const size_t n1 = n > 1 ? (size_t)n - 1 : 1;
-    const size_t nn = (size_t)n;
-    char *p = (char *)(((uintptr_t)base + 255) & ~(uintptr_t)255);
+    uintptr_t p = (base + 255) & ~(uintptr_t)255;
+    const uintptr_t start = base;
     auto take = [&](size_t bytes) {
-        char *q = p;
+        uintptr_t q = p;
         p += (bytes + 255) & ~(size_t)255;
         return (void *)q;
     };
+    Scratch T;
+    T.cnt = (int *)take(sizeof(int) * C_COUNT);
+    T.cnt64 = (unsigned long long *)take(sizeof(unsigned long long) * C64_COUNT);
+    T.perm = (int *)take(sizeof(int) * n1);
+    T.spos = (int *)take(sizeof(int) * n1);
+    T.kind = (int *)take(sizeof(int) * n1);
+    T.run_s0 = (int *)take(sizeof(int) * n1);
+    T.run_R = (double *)take(sizeof(double) * 2 * n1);
+    T.pd = (double *)take(sizeof(double) * n1);
+    T.pz = (double *)take(sizeof(double) * n1);
+    T.pz2 = (double *)take(sizeof(double) * n1);
+    T.pdh = (float *)take(sizeof(float) * n1);
+    T.pdl = (float *)take(sizeof(float) * n1);
+    T.pz2f = (float *)take(sizeof(float) * n1);
+    T.fscale = (double *)take(sizeof(double) * 2);
+    T.prow = (int *)take(sizeof(int) * n1);
+    T.drow = (int *)take(sizeof(int) * n1);
+    T.dval = (double *)take(sizeof(double) * n1);
+    T.es_sigma = (double *)take(sizeof(double) * nn);
+    T.es_mu = (double *)take(sizeof(double) * nn);
+    T.es_lam = (double *)take(sizeof(double) * nn);
+    T.es_b = (double *)take(sizeof(double) * nn);
+    T.es_Kb = (double *)take(sizeof(double) * nn);
+    T.es_Knu = (double *)take(sizeof(double) * nn);
+    T.es_fixshift = (double *)take(sizeof(double) * nn);
+    T.es_pole = (int *)take(sizeof(int) * nn);
+    T.es_iters = (int *)take(sizeof(int) * nn);
+    T.es_flags = (int *)take(sizeof(int) * nn);
+    T.es_fixpole = (int *)take(sizeof(int) * nn);
+    T.fixlist = (int *)take(sizeof(int) * nn);
+    T.pos = (int *)take(sizeof(int) * nn);
+    if (S) *S = T;
+    return (size_t)(p - start);
+}
+
+// bytes to request: the layout from a 256-aligned base, plus room to align
+size_t arrow_scratch_bytes(int n) { return layout(0, n, nullptr) + 256; }
+
+Scratch carve_scratch(void *base, int n) {
     Scratch S;
-    S.cnt = (int *)take(sizeof(int) * C_COUNT);
-    S.cnt64 = (unsigned long long *)take(sizeof(unsigned long long) * C64_COUNT);
-    S.perm = (int *)take(sizeof(int) * n1);
-    S.spos = (int *)take(sizeof(int) * n1);
-    S.kind = (int *)take(sizeof(int) * n1);
-    S.run_s0 = (int *)take(sizeof(int) * n1);
-    S.run_R = (double *)take(sizeof(double) * 2 * n1);
-    S.pd = (double *)take(sizeof(double) * n1);
-    S.pz = (double *)take(sizeof(double) * n1);
-    S.pz2 = (double *)take(sizeof(double) * n1);
-    S.prow = (int *)take(sizeof(int) * n1);
-    S.drow = (int *)take(sizeof(int) * n1);
-    S.dval = (double *)take(sizeof(double) * n1);
-    S.es_sigma = (double *)take(sizeof(double) * nn);
-    S.es_mu = (double *)take(sizeof(double) * nn);
-    S.es_lam = (double *)take(sizeof(double) * nn);
-    S.es_b = (double *)take(sizeof(double) * nn);
-    S.es_Kb = (double *)take(sizeof(double) * nn);
-    S.es_Knu = (double *)take(sizeof(double) * nn);
-    S.es_fixshift = (double *)take(sizeof(double) * nn);
-    S.es_pole = (int *)take(sizeof(int) * nn);
-    S.es_iters = (int *)take(sizeof(int) * nn);
-    S.es_flags = (int *)take(sizeof(int) * nn);
-    S.es_fixpole = (int *)take(sizeof(int) * nn);
-    S.fixlist = (int *)take(sizeof(int) * nn);
-    S.pos = (int *)take(sizeof(int) * nn);
+    layout((uintptr_t)base, n, &S);
     return S;
 }
 

@@ -38,6 +38,8 @@ struct Scratch {
     int *run_s0;    // folded row: sorted position where its run starts
     double *run_R;  // folded row: R_{m-1}, R_m
     double *pd, *pz, *pz2;  // reduced poles / spikes / fl(spike^2)
+    float *pdh, *pdl, *pz2f;  // FP32 copies: pole*ds split hi+lo, spike^2*zs
+    double *fscale;           // ds, zs (powers of two)
     int *prow;      // reduced pole -> input row of its head
     int *drow;      // deflated rows in sorted order
     double *dval;   // their pole values

@@ -47,6 +47,12 @@ struct ArrowPoles {
     const double *__restrict__ pz;   // zeta_j > 0
     const double *__restrict__ pz2;  // fl(zeta_j^2)
     double alpha;
+    // FP32 copies for the opening bracket: poles split hi + lo after scaling
+    // by ds, and zeta^2 scaled by zs (ds, zs powers of two); null when absent
+    const float *__restrict__ pdh;
+    const float *__restrict__ pdl;
+    const float *__restrict__ pz2f;
+    double ds, zs;
 
     __device__ __forceinline__ double pole(int j) const { return __ldg(pd + j); }
     // p_j - shift in double; `i` is the shift's pole index (-1: not a pole)
@@ -64,7 +70,51 @@ struct ArrowPoles {
     }
     // a = alpha - shift, exact
     __device__ __forceinline__ dd a_dd(double shift, int) const { return two_sum(alpha, -shift); }
+    // scaled shifted difference (p_j - shift) * ds in FP32 from the hi/lo split
+    __device__ __forceinline__ float shifted_f32(int j, float sh, float sl) const {
+        return (__ldg(pdh + j) - sh) + (__ldg(pdl + j) - sl);
+    }
+    __device__ __forceinline__ float z2f(int j) const { return __ldg(pz2f + j); }
+    __device__ __forceinline__ bool has_f32() const { return pdh != nullptr; }
 };
+
+__device__ __forceinline__ float rcp_f32(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// FP32 analogue of secular_sum on scaled data:
+// T(y) = sum_{j != skip} zz_j / (D_j (1 - y D_j)),  D_j = (p_j - shift) ds sc,
+// zz_j = zeta_j^2 zs.  With x = s y and s = ds sc:  S(x) = s T(y) / zs.
+template <class P>
+__device__ __forceinline__ float secular_sum_f32(const P &R, float sh, float sl, float sc,
+                                                 int skip, float y, int lane) {
+    float acc0 = 0.f, acc1 = 0.f;
+    int j = lane;
+    for (; j + 32 < R.m; j += 64) {
+        if (j != skip) {
+            const float D = R.shifted_f32(j, sh, sl) * sc;
+            const float t = fmaf(-y, D, 1.f);
+            acc0 = fmaf(R.z2f(j), rcp_f32(D * t), acc0);
+        }
+        const int j2 = j + 32;
+        if (j2 != skip) {
+            const float D = R.shifted_f32(j2, sh, sl) * sc;
+            const float t = fmaf(-y, D, 1.f);
+            acc1 = fmaf(R.z2f(j2), rcp_f32(D * t), acc1);
+        }
+    }
+    if (j < R.m && j != skip) {
+        const float D = R.shifted_f32(j, sh, sl) * sc;
+        const float t = fmaf(-y, D, 1.f);
+        acc0 = fmaf(R.z2f(j), rcp_f32(D * t), acc0);
+    }
+    float v = acc0 + acc1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
 
 // S(x) = sum_{j != skip} zeta_j^2 / (delta_j (1 - x delta_j)), delta_j = p_j - shift
 template <class P>
@@ -170,6 +220,53 @@ __device__ __forceinline__ PassA pass_a(const P &R, double shift, int skip, doub
     return A;
 }
 
+// F(x) of the inverse's Pick function in FP64 (one evaluation, all terms)
+template <class P>
+__device__ __forceinline__ double pick_inverse_f64(const P &R, double sigma, int i, double b,
+                                                   double c, double x, int lane) {
+    const double S = secular_sum(R, sigma, i, x, lane);
+    return (b - x) - c * (S - rcp(x));
+}
+
+// Narrow [left, right] (which holds the zero nu of F) with FP32 bisection, then
+// verify the new ends in FP64: F(l) > 0 >= F(r).  Returns false (bracket
+// unchanged) when the FP32 data cannot represent the problem or the check fails.
+template <class P>
+__device__ bool fp32_bracket(const P &R, double sigma, int i, double b, double c, double &left,
+                             double &right, int lane) {
+    const double big = fmax(fabs(left), fabs(right));
+    if (!(big > 0.0) || !isfinite(big)) return false;
+    const double s = ldexp(1.0, ilogb(big));          // x = s y, |y| <= 2
+    const double scd = s / R.ds;                        // D_j = (p_j - sigma) ds * scd
+    if (!(scd > 0x1p-120 && scd < 0x1p120)) return false;
+    const double ss = sigma * R.ds;
+    const float sh = (float)ss;
+    const float sl = (float)(ss - (double)sh);
+    if (!isfinite(sh)) return false;
+    const float sc = (float)scd;
+    const double K = c * s / R.zs;                      // F = G(x) - K T(y)
+    double l = left, r = right;
+    for (int it = 0; it < 80; ++it) {
+        const double mid = 0.5 * (l + r);
+        if (r - l <= 0x1p-20 * fabs(mid)) break;
+        const float y = (float)(mid / s);
+        const double x = s * (double)y;                 // the point actually evaluated
+        if (!(x > l && x < r)) break;
+        const float T = secular_sum_f32(R, sh, sl, sc, i, y, lane);
+        const double F = (b - x) + c * rcp(x) - K * (double)T;
+        if (F > 0.0) l = x;
+        else r = x;
+    }
+    // widen by the bracket width and check both ends in FP64
+    const double w = r - l;
+    const double L = fmax(left, l - w), Rr = fmin(right, r + w);
+    if (L > left && !(pick_inverse_f64(R, sigma, i, b, c, L, lane) > 0.0)) return false;
+    if (Rr < right && !(pick_inverse_f64(R, sigma, i, b, c, Rr, lane) <= 0.0)) return false;
+    left = L;
+    right = Rr;
+    return true;
+}
+
 // Algorithm 2 + 3 for the shift pole i on `side`, then lambda = sigma + 1/nu.
 template <class P>
 __device__ EigResult solve_shifted(const P &R, int i, int side, const SolveOpts &o, int lane) {
@@ -195,6 +292,14 @@ __device__ EigResult solve_shifted(const P &R, int i, int side, const SolveOpts 
         right = fmin(A.pmin, 0.0);
         left = fmin(fmin(A.lo, -wz), b - norm1);
     }
+    if (o.precision == 1 && R.has_f32()) {
+        // FP32 opening bracket on a power-of-two rescaled copy (x = s y), then
+        // an FP64 check of both ends; on failure keep the Gershgorin bracket.
+        res.flags = 0;
+        if (!fp32_bracket(R, sigma, i, b, c, left, right, lane)) res.flags = 64;
+    } else {
+        res.flags = 0;
+    }
     int it = 0;
     double mid = 0.5 * (left + right);
     while (right - left > TWO_EPS * fabs(mid) && it < o.max_iter) {
@@ -211,7 +316,7 @@ __device__ EigResult solve_shifted(const P &R, int i, int side, const SolveOpts 
     res.lam = sigma + res.mu;
     res.pole = i;
     res.iters = it;
-    res.flags = (it >= o.max_iter) ? 16 : 0;
+    res.flags |= (it >= o.max_iter) ? 16 : 0;
     return res;
 }
 

@@ -204,3 +204,58 @@ def test_graded_full_size_sampled(ae):
     # orthogonality of the sampled columns
     G = V[:, ks].T @ V[:, ks] - np.eye(ks.size)
     assert np.abs(G).max() <= 10 * n * 2.0 ** -53
+
+
+# ---------------------------------------------------------------------------
+# precision variant: FP32 opening bracket, FP64 check and finish
+# ---------------------------------------------------------------------------
+def _opts32(ae):
+    return ae.default_opts(precision=ae.AE_FP32_BRACKET)
+
+
+@pytest.mark.parametrize("case", ["ex1", "ex2", "ex3", "uniform1000", "graded3001", "qdot",
+                                  "mirrored", "deflation"])
+def test_fp32_bracket_parity(ae, case):
+    if case.startswith("ex"):
+        d, z, a = W.paper_example(int(case[2]))
+    elif case == "uniform1000":
+        d, z, a = W.uniform_arrow(1000, seed=0)
+    elif case == "graded3001":
+        d, z, a = W.graded_arrow(3001, seed=13)
+    elif case == "qdot":
+        d, z, a = W.quantum_dot_like(2501)
+    elif case == "mirrored":
+        d, z, a = W.mirrored_arrow(41)
+    else:
+        d = np.array([0.5, 3.0, 2.0, 3.0, -1.0, 3.0, 2.0, 7.5, -1.0, 0.25])
+        z = np.array([0.5, -1.0, 0.0, 2.0, 1.0, -0.0, 0.25, -3.0, 0.125, 1.5])
+        a = 0.3
+    g, o = check_full(ae, d, z, a, f"fp32 bracket {case}", opts=_opts32(ae))
+    info = g["info"]
+    assert info["n_capped"] == 0
+
+
+def test_fp32_bracket_saves_fp64_steps(ae):
+    d, z, a = W.graded_arrow(4000, seed=17)
+    g64 = gpu_solve(ae, d, z, a, info=True)
+    g32 = gpu_solve(ae, d, z, a, info=True, opts=_opts32(ae))
+    i64, i32 = g64["info"], g32["info"]
+    # FP64 evaluations per eigenpair drop by at least a quarter
+    assert i32["total_iter"] < 0.75 * i64["total_iter"]
+    assert i32["n_fp32_fallback"] <= 0.01 * len(d)
+
+
+def test_fp32_bracket_full_size_sampled(ae):
+    n = 16384
+    d, z, a = W.graded_arrow(n, seed=1)
+    g = gpu_solve(ae, d, z, a, info=True, diag=True, opts=_opts32(ae))
+    lam, V = g["lam"], g["V"]
+    assert np.all(lam[:-1] >= d) and np.all(d >= lam[1:])
+    flags = g["diag"]["flags"]
+    fixed = np.nonzero(flags & (ae.FLAG_NEARZERO | ae.FLAG_OTHERPOLE | ae.FLAG_DPR1SHIFT))[0]
+    fb = np.nonzero(flags & ae.FLAG_FP32_FALLBACK)[0]
+    rng = np.random.default_rng(8)
+    ks = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1],
+                                   rng.choice(n, 96, replace=False), fixed[:32], fb[:32]]))
+    o = oracle.arrow_eig(d, z, a, ks=ks)
+    assert_parity(lam[ks], V[:, ks], o, n, cols=ks, what="fp32 bracket graded n=16384")
