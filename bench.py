@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--precision", default="fp32", choices=["fp64", "fp32"],
+                   help="headline form: fp32 = FP32 opening bracket + FP64 finish")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -114,6 +115,7 @@ def eig_kernel_flops(n, ncomp, total_iter, fix_iter):
 
 
 def cpu_baseline(d, z, alpha, n, seconds):
+    """Time the oracle on a sample; also return its results for an error check."""
     import oracle
     oracle.build_oracle()
     # size the sample from a short calibration run
@@ -124,11 +126,22 @@ def cpu_baseline(d, z, alpha, n, seconds):
     cnt = int(max(16, min(n, seconds / max(per, 1e-9))))
     ks = np.unique(np.linspace(0, n - 1, cnt).astype(np.int64))
     t0 = time.perf_counter()
-    oracle.arrow_eig(d, z, alpha, ks=ks)
+    res = oracle.arrow_eig(d, z, alpha, ks=ks)
     dt = time.perf_counter() - t0
-    return {"value": ks.size / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{ks.size} of {n} eigenpairs (evenly spaced) with vectors, "
-                      f"double-double oracle, {dt:.1f} s"}
+    return ({"value": ks.size / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+             "sample": f"{ks.size} of {n} eigenpairs (evenly spaced) with vectors, "
+                       f"double-double oracle, {dt:.1f} s"}, ks, res)
+
+
+def max_err_neps(lam, Vcols, res, n):
+    """Max relative error of GPU results vs the oracle sample, in units of n eps64."""
+    eps = 2.0 ** -53
+    tol = 10 * n * eps
+    scale = np.maximum(np.abs(res["lam"]), 4 * res["abserr"] / tol)
+    el = np.max(np.abs(lam - res["lam"]) / scale) / (n * eps)
+    ev = np.max(np.abs(Vcols - res["V"]) /
+                np.maximum(np.abs(res["V"]), np.finfo(float).tiny)) / (n * eps)
+    return {"lambda": float(el), "vectors": float(ev), "bound": 10.0}
 
 
 def run_reference(args, rank, world):
@@ -189,38 +202,46 @@ def main():
     lam = torch.empty(n, dtype=torch.float64, device=dev)
     V = torch.empty((n, n), dtype=torch.float64, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    prec = arrowhead.AE_FP64 if args.precision == "fp64" else arrowhead.AE_FP32_BRACKET
-    opts = arrowhead.default_opts(precision=prec, profile=1)
     stream = torch.cuda.current_stream()
 
-    def step():
-        return arrowhead.arrow_eig(dt, zt, alpha, opts=opts, info=True,
-                                   out={"lam": lam, "V": V}, stream=stream)
+    def timed(prec):
+        opts = arrowhead.default_opts(precision=prec, profile=1)
 
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    infos = []
-    with Clocks(local) as clk:
+        def step():
+            return arrowhead.arrow_eig(dt, zt, alpha, opts=opts, info=True,
+                                       out={"lam": lam, "V": V}, stream=stream)
+
+        for _ in range(max(args.warmup, 0)):
+            step()
         torch.cuda.synchronize()
-        for i in range(args.steps):
-            flush.fill_(i & 0xff)                 # evict L2 between steps
-            starts[i].record(stream)
-            infos.append(step()["info"])
-            ends[i].record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        if world > 1:
+            dist.barrier()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        infos = []
+        with Clocks(local) as clk:
+            torch.cuda.synchronize()
+            for i in range(args.steps):
+                flush.fill_(i & 0xff)                 # evict L2 between steps
+                starts[i].record(stream)
+                infos.append(step()["info"])
+                ends[i].record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        total = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+        if world > 1:
+            t = torch.tensor([total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total, infos, clk
+
+    P64, P32 = arrowhead.AE_FP64, arrowhead.AE_FP32_BRACKET
+    primary = P32 if args.precision == "fp32" else P64
+    other = P64 if primary == P32 else P32
+    # the other form first, so lam/V hold the headline form's results at the end
+    total_o, infos_o, _ = timed(other)
+    total_ms, infos, clk = timed(primary)
     value = world * n * args.steps / (total_ms / 1e3)
     info = infos[-1]
     eig_ms = float(np.mean([x["ms_eig"] for x in infos]))
@@ -237,11 +258,14 @@ def main():
         zh = torch.as_tensor(z).pin_memory()
         lh = torch.empty(n, dtype=torch.float64).pin_memory()
         Vh = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        arrowhead.arrow_eig_host(dh, zh, alpha, out={"lam": lh, "V": Vh}, stream=stream)
+        eopts = arrowhead.default_opts(precision=primary)
+        arrowhead.arrow_eig_host(dh, zh, alpha, opts=eopts, out={"lam": lh, "V": Vh},
+                                 stream=stream)
         t0 = time.perf_counter()
         ne = max(2, min(args.steps, 3))
         for _ in range(ne):
-            arrowhead.arrow_eig_host(dh, zh, alpha, out={"lam": lh, "V": Vh}, stream=stream)
+            arrowhead.arrow_eig_host(dh, zh, alpha, opts=eopts, out={"lam": lh, "V": Vh},
+                                     stream=stream)
         te = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([te], device=dev)
@@ -252,17 +276,29 @@ def main():
 
     if rank == 0:
         cpu = None
+        err = None
         if world == 1 and not args.no_cpu:
-            cpu = cpu_baseline(d, z, alpha, n, args.cpu_seconds)
+            cpu, ks, ores = cpu_baseline(d, z, alpha, n, args.cpu_seconds)
+            kt = torch.as_tensor(ks, device=dev)
+            err = max_err_neps(lam[kt].cpu().numpy(), V[kt].t().cpu().numpy(), ores, n)
+        name = {P64: "fp64", P32: "fp32_bracket"}
+        variants = {}
+        for prec, tot, inf in ((primary, total_ms, infos), (other, total_o, infos_o)):
+            variants[name[prec]] = {
+                "value": world * n * args.steps / (tot / 1e3), "ms_per_step": tot / args.steps,
+                "ms_eig": float(np.mean([x["ms_eig"] for x in inf])),
+                "fp64_steps_per_eigenpair": inf[-1]["total_iter"] / n,
+                "fp32_fallbacks": inf[-1]["n_fp32_fallback"]}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"graded arrowhead n={n}: all eigenpairs + full V",
-                           "n": n, "precision": args.precision,
+                           "n": n, "precision": name[primary],
                            "l2": "512 MiB write between steps (L2 flush)",
                            "parallelism": f"{world} independent instances"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+                "max_err_neps": err, "variants": variants,
                 "clocks": clk.summary(), "gpu_launches": LAUNCHES_PER_STEP * args.steps,
                 "phases_ms": {k: float(np.mean([x[k] for x in infos]))
                               for k in ("ms_reduce", "ms_eig", "ms_fix", "ms_vectors")},

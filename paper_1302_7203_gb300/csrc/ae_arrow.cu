@@ -249,9 +249,10 @@ __global__ void __launch_bounds__(256) k_eig(double alpha, Scratch S, SolveOpts 
         if (m == 0) {
             res = {alpha, 0.0, alpha, NAN, 0.0, -1, 0, 0};
         } else {
+            const WarpTeam T{lane};
             int i, side;
-            select_shift(R, k, lane, i, side);
-            res = solve_shifted(R, i, side, o, lane);
+            select_shift(R, T, k, i, side);
+            res = solve_shifted(R, T, i, side, o);
         }
         if (lane == 0) {
             store_result(S, k, res);
@@ -324,34 +325,39 @@ __global__ void k_fix_decide(Scratch S, double knu_max) {
     }
 }
 
+// Remedy solves: one CTA (8 warps) per listed eigenpair, so that the few
+// eigenpairs that need one still fill the GPU.
 __global__ void __launch_bounds__(256) k_fix_solve(double alpha, Scratch S, SolveOpts o) {
-    const int lane = threadIdx.x & 31;
+    __shared__ double red[16];
+    __shared__ int ticket;
     const int m = S.cnt[C_M];
     const int nfix = S.cnt[C_NFIX];
     const ArrowPoles R = {m,       S.pd,   S.pz,   S.pz2,          alpha,
                           S.pdh,   S.pdl,  S.pz2f, S.fscale[0],    S.fscale[1]};
+    const CtaTeam<8> T{(int)threadIdx.x, red};
     for (;;) {
-        int w = 0;
-        if (lane == 0) w = atomicAdd(S.cnt + C_WORK2, 1);
-        w = __shfl_sync(FULL, w, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) ticket = atomicAdd(S.cnt + C_WORK2, 1);
+        __syncthreads();
+        const int w = ticket;
         if (w >= nfix) break;
         const int k = S.fixlist[w];
         const int f = S.es_flags[k];
         EigResult res;
         if (f & AE_FLAG_NEARZERO) {
-            res = solve_dpr1_shift(R, 0.0, o, lane);
+            res = solve_dpr1_shift(R, T, 0.0, o);
         } else if (f & AE_FLAG_OTHERPOLE) {
             const int io = S.es_fixpole[k];
             const int side = io < S.es_pole[k] ? -1 : +1;   // other pole above -> lambda below it
-            res = solve_shifted(R, io, side, o, lane);
+            res = solve_shifted(R, T, io, side, o);
         } else {
-            res = solve_dpr1_shift(R, S.es_fixshift[k], o, lane);
+            res = solve_dpr1_shift(R, T, S.es_fixshift[k], o);
         }
         // the result must stay in the eigenvalue's interlacing interval
         const double lo = k < m ? R.pole(k) : -INFINITY;
         const double hi = k > 0 ? R.pole(k - 1) : INFINITY;
         const bool ok = (res.lam >= lo && res.lam <= hi) && isfinite(res.lam);
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             if (ok) {
                 // b and K_b stay those of Algorithm 1's shift pole
                 res.b = S.es_b[k];
@@ -595,7 +601,8 @@ cudaError_t launch_arrow(int n, const double *d, const double *z, double alpha,
     if (ro.ev[2]) cudaEventRecord(ro.ev[2], st);
     if (ro.fixup) {
         k_fix_decide<<<(n + 255) / 256, 256, 0, st>>>(S, ro.knu_max);
-        k_fix_solve<<<grid, 256, 0, st>>>(alpha, S, so);
+        int fgrid = n < sms * 4 ? n : sms * 4;
+        k_fix_solve<<<fgrid, 256, 0, st>>>(alpha, S, so);
     }
     if (ro.ev[3]) cudaEventRecord(ro.ev[3], st);
     k_place<<<(n + 255) / 256, 256, 0, st>>>(S);

@@ -1,8 +1,9 @@
-// ae_solver.cuh -- one eigenpair per warp: shift selection (Algorithm 1),
-// the inverse of the shifted arrowhead with its element b in double-double
-// (Algorithm 2, Eq. invAi / b_ob, Theorem 6), bisection for the inverse's
-// extreme eigenvalue (Algorithm 3) and the Remark 1 / Remark 2(b) solve on a
-// DPR1 inverse (A - sigma I)^{-1}.
+// ae_solver.cuh -- one eigenpair per team (a warp, or a CTA of NW warps):
+// shift selection (Algorithm 1), the inverse of the shifted arrowhead with its
+// element b in double-double (Algorithm 2, Eq. invAi / b_ob, Theorem 6),
+// bisection for the inverse's extreme eigenvalue (Algorithm 3), optionally
+// opened by an FP32 bracket, and the Remark 1 / Remark 2(b) solve on the DPR1
+// inverse (A - sigma I)^{-1}.
 //
 // Notation (0-based): reduced poles p_0 > p_1 > ... > p_{m-1}, spikes
 // zeta_j > 0, corner alpha; eigenvalue k (k = 0..m) lies in (p_k, p_{k-1}).
@@ -19,6 +20,9 @@
 //     S(x) = sum_{j!=i} zeta_j^2 / (delta_j (1 - x delta_j)).
 // All terms of S(x) - 1/x have one sign on the side being searched, so the only
 // cancellation is the final one, exactly as in the paper's evaluation.
+//
+// Every reduction has a fixed order, so a solve is bit-reproducible for a
+// given team shape.
 #pragma once
 #include "ae_device.cuh"
 
@@ -40,7 +44,82 @@ struct EigResult {
     int flags;
 };
 
-// Poles and spikes of a reduced arrowhead held in device memory.
+// ---------------------------------------------------------------------------
+// teams
+// ---------------------------------------------------------------------------
+struct WarpTeam {
+    int rank;                       // lane
+    static constexpr int size = 32;
+    __device__ __forceinline__ double sum(double v) const { return warp_sum(v); }
+    __device__ __forceinline__ float sumf(float v) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        return v;
+    }
+    __device__ __forceinline__ dd sum(dd v) const { return warp_sum_dd(v); }
+    __device__ __forceinline__ double max(double v) const { return warp_max(v); }
+    __device__ __forceinline__ double min(double v) const { return warp_min(v); }
+};
+
+// A CTA of NW warps; `red` points at 2*NW doubles of shared memory.
+template <int NW>
+struct CtaTeam {
+    int rank;                       // threadIdx.x
+    double *red;
+    static constexpr int size = 32 * NW;
+    __device__ __forceinline__ double sum(double v) const {
+        v = warp_sum(v);
+        __syncthreads();
+        if ((rank & 31) == 0) red[rank >> 5] = v;
+        __syncthreads();
+        double r = red[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) r += red[w];
+        return r;
+    }
+    __device__ __forceinline__ float sumf(float v) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        return (float)sum((double)v);
+    }
+    __device__ __forceinline__ dd sum(dd v) const {
+        v = warp_sum_dd(v);
+        __syncthreads();
+        if ((rank & 31) == 0) {
+            red[rank >> 5] = v.hi;
+            red[NW + (rank >> 5)] = v.lo;
+        }
+        __syncthreads();
+        dd r = {red[0], red[NW]};
+#pragma unroll
+        for (int w = 1; w < NW; ++w) r = dd_add(r, dd{red[w], red[NW + w]});
+        return r;
+    }
+    __device__ __forceinline__ double max(double v) const {
+        v = warp_max(v);
+        __syncthreads();
+        if ((rank & 31) == 0) red[rank >> 5] = v;
+        __syncthreads();
+        double r = red[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) r = fmax(r, red[w]);
+        return r;
+    }
+    __device__ __forceinline__ double min(double v) const {
+        v = warp_min(v);
+        __syncthreads();
+        if ((rank & 31) == 0) red[rank >> 5] = v;
+        __syncthreads();
+        double r = red[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) r = fmin(r, red[w]);
+        return r;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// poles and spikes of a reduced arrowhead held in device memory
+// ---------------------------------------------------------------------------
 struct ArrowPoles {
     int m;
     const double *__restrict__ pd;   // poles, strictly decreasing
@@ -84,21 +163,51 @@ __device__ __forceinline__ float rcp_f32(float x) {
     return r;
 }
 
-// FP32 analogue of secular_sum on scaled data:
+// ---------------------------------------------------------------------------
+// O(n) passes
+// ---------------------------------------------------------------------------
+// S(x) = sum_{j != skip} zeta_j^2 / (delta_j (1 - x delta_j)), delta_j = p_j - shift
+template <class P, class Team>
+__device__ __forceinline__ double secular_sum(const P &R, const Team &T, double shift, int skip,
+                                              double x) {
+    double acc0 = 0.0, acc1 = 0.0;
+    int j = T.rank;
+    for (; j + Team::size < R.m; j += 2 * Team::size) {
+        if (j != skip) {
+            const double dj = R.shifted(j, shift, skip);
+            const double t = fma(-x, dj, 1.0);
+            acc0 = fma(R.z2(j), rcp(dj * t), acc0);
+        }
+        const int j2 = j + Team::size;
+        if (j2 != skip) {
+            const double dj = R.shifted(j2, shift, skip);
+            const double t = fma(-x, dj, 1.0);
+            acc1 = fma(R.z2(j2), rcp(dj * t), acc1);
+        }
+    }
+    if (j < R.m && j != skip) {
+        const double dj = R.shifted(j, shift, skip);
+        const double t = fma(-x, dj, 1.0);
+        acc0 = fma(R.z2(j), rcp(dj * t), acc0);
+    }
+    return T.sum(acc0 + acc1);
+}
+
+// FP32 analogue on scaled data:
 // T(y) = sum_{j != skip} zz_j / (D_j (1 - y D_j)),  D_j = (p_j - shift) ds sc,
 // zz_j = zeta_j^2 zs.  With x = s y and s = ds sc:  S(x) = s T(y) / zs.
-template <class P>
-__device__ __forceinline__ float secular_sum_f32(const P &R, float sh, float sl, float sc,
-                                                 int skip, float y, int lane) {
+template <class P, class Team>
+__device__ __forceinline__ float secular_sum_f32(const P &R, const Team &T, float sh, float sl,
+                                                 float sc, int skip, float y) {
     float acc0 = 0.f, acc1 = 0.f;
-    int j = lane;
-    for (; j + 32 < R.m; j += 64) {
+    int j = T.rank;
+    for (; j + Team::size < R.m; j += 2 * Team::size) {
         if (j != skip) {
             const float D = R.shifted_f32(j, sh, sl) * sc;
             const float t = fmaf(-y, D, 1.f);
             acc0 = fmaf(R.z2f(j), rcp_f32(D * t), acc0);
         }
-        const int j2 = j + 32;
+        const int j2 = j + Team::size;
         if (j2 != skip) {
             const float D = R.shifted_f32(j2, sh, sl) * sc;
             const float t = fmaf(-y, D, 1.f);
@@ -110,42 +219,13 @@ __device__ __forceinline__ float secular_sum_f32(const P &R, float sh, float sl,
         const float t = fmaf(-y, D, 1.f);
         acc0 = fmaf(R.z2f(j), rcp_f32(D * t), acc0);
     }
-    float v = acc0 + acc1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-
-// S(x) = sum_{j != skip} zeta_j^2 / (delta_j (1 - x delta_j)), delta_j = p_j - shift
-template <class P>
-__device__ __forceinline__ double secular_sum(const P &R, double shift, int skip, double x,
-                                              int lane) {
-    double acc0 = 0.0, acc1 = 0.0;
-    int j = lane;
-    for (; j + 32 < R.m; j += 64) {
-        if (j != skip) {
-            double dj = R.shifted(j, shift, skip);
-            double t = fma(-x, dj, 1.0);
-            acc0 = fma(R.z2(j), rcp(dj * t), acc0);
-        }
-        int j2 = j + 32;
-        if (j2 != skip) {
-            double dj = R.shifted(j2, shift, skip);
-            double t = fma(-x, dj, 1.0);
-            acc1 = fma(R.z2(j2), rcp(dj * t), acc1);
-        }
-    }
-    if (j < R.m && j != skip) {
-        double dj = R.shifted(j, shift, skip);
-        double t = fma(-x, dj, 1.0);
-        acc0 = fma(R.z2(j), rcp(dj * t), acc0);
-    }
-    return warp_sum(acc0 + acc1);
+    return T.sumf(acc0 + acc1);
 }
 
 // Algorithm 1, first part: the shift pole i and the side (+1: lambda > p_i).
-template <class P>
-__device__ __forceinline__ void select_shift(const P &R, int k, int lane, int &i, int &side) {
+template <class P, class Team>
+__device__ __forceinline__ void select_shift(const P &R, const Team &T, int k, int &i,
+                                             int &side) {
     const int m = R.m;
     if (k == 0) {
         i = 0; side = +1;
@@ -156,9 +236,9 @@ __device__ __forceinline__ void select_shift(const P &R, int k, int lane, int &i
         const double middle = 0.5 * R.shifted(k - 1, sk, k);
         const dd a = R.a_dd(sk, k);
         double acc = 0.0;
-        for (int j = lane; j < m; j += 32)
+        for (int j = T.rank; j < m; j += Team::size)
             acc = fma(R.z2(j), rcp(R.shifted(j, sk, k) - middle), acc);
-        const double F = (a.hi - middle) - warp_sum(acc);
+        const double F = (a.hi - middle) - T.sum(acc);
         if (F < 0.0) { i = k; side = +1; }
         else { i = k - 1; side = -1; }
     }
@@ -179,13 +259,13 @@ struct PassA {
     double usq;         // sum zeta_j^2 / delta_j^2
 };
 
-template <class P>
-__device__ __forceinline__ PassA pass_a(const P &R, double shift, int skip, double wscale,
-                                        int lane) {
+template <class P, class Team>
+__device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift, int skip,
+                                        double wscale) {
     dd s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
     double pmax = -INFINITY, pmin = INFINITY, up = -INFINITY, lo = INFINITY, wsum = 0.0,
            usq = 0.0;
-    for (int j = lane; j < R.m; j += 32) {
+    for (int j = T.rank; j < R.m; j += Team::size) {
         if (j == skip) continue;
         const dd del = R.shifted_dd(j, shift, skip);
         const dd t = dd_div(R.z2_dd(j), del);
@@ -200,15 +280,15 @@ __device__ __forceinline__ PassA pass_a(const P &R, double shift, int skip, doub
         wsum += aw;
         usq = fma(aw, aw, usq);
     }
-    s1 = warp_sum_dd(s1);
-    s2 = warp_sum_dd(s2);
+    s1 = T.sum(s1);
+    s2 = T.sum(s2);
     PassA A;
-    A.pmax = warp_max(pmax);
-    A.pmin = warp_min(pmin);
-    A.up = warp_max(up);
-    A.lo = warp_min(lo);
-    A.wsum = warp_sum(wsum);
-    A.usq = warp_sum(usq);
+    A.pmax = T.max(pmax);
+    A.pmin = T.min(pmin);
+    A.up = T.max(up);
+    A.lo = T.min(lo);
+    A.wsum = T.sum(wsum);
+    A.usq = T.sum(usq);
     const dd a = R.a_dd(shift, skip);   // alpha - shift
     if (a.hi < 0.0) {                   // -a > 0: P = -a + S1, Q = -S2
         A.P = dd_add_same(dd_neg(a), s1);
@@ -220,31 +300,29 @@ __device__ __forceinline__ PassA pass_a(const P &R, double shift, int skip, doub
     return A;
 }
 
-// F(x) of the inverse's Pick function in FP64 (one evaluation, all terms)
-template <class P>
-__device__ __forceinline__ double pick_inverse_f64(const P &R, double sigma, int i, double b,
-                                                   double c, double x, int lane) {
-    const double S = secular_sum(R, sigma, i, x, lane);
-    return (b - x) - c * (S - rcp(x));
-}
-
-// Narrow [left, right] (which holds the zero nu of F) with FP32 bisection, then
-// verify the new ends in FP64: F(l) > 0 >= F(r).  Returns false (bracket
-// unchanged) when the FP32 data cannot represent the problem or the check fails.
-template <class P>
-__device__ bool fp32_bracket(const P &R, double sigma, int i, double b, double c, double &left,
-                             double &right, int lane) {
+// ---------------------------------------------------------------------------
+// FP32 opening bracket
+// ---------------------------------------------------------------------------
+// Narrow [left, right] (which holds the zero of a function Phi) with FP32
+// bisection, then verify the new ends in FP64.  Phi(x) = G(x) - K T(y), x = s y,
+// where G is the FP64 part (shift, b or 1, the 1/x term) and T the FP32 sum,
+// K = K_over_s * s / zs.  `dir` = +1 when Phi > 0 below the zero, -1 when
+// above.  Returns false (bracket unchanged) when the FP32 data cannot
+// represent the problem or the FP64 check of an end fails.
+template <class P, class Team, class G64, class F64>
+__device__ bool fp32_bracket(const P &R, const Team &T, double shift, int skip, double K_over_s,
+                             int dir, G64 g64, F64 f64, double &left, double &right) {
     const double big = fmax(fabs(left), fabs(right));
     if (!(big > 0.0) || !isfinite(big)) return false;
     const double s = ldexp(1.0, ilogb(big));          // x = s y, |y| <= 2
-    const double scd = s / R.ds;                        // D_j = (p_j - sigma) ds * scd
+    const double scd = s / R.ds;                        // D_j = (p_j - shift) ds * scd
     if (!(scd > 0x1p-120 && scd < 0x1p120)) return false;
-    const double ss = sigma * R.ds;
+    const double ss = shift * R.ds;
     const float sh = (float)ss;
     const float sl = (float)(ss - (double)sh);
     if (!isfinite(sh)) return false;
     const float sc = (float)scd;
-    const double K = c * s / R.zs;                      // F = G(x) - K T(y)
+    const double K = K_over_s * s / R.zs;
     double l = left, r = right;
     for (int it = 0; it < 80; ++it) {
         const double mid = 0.5 * (l + r);
@@ -252,30 +330,40 @@ __device__ bool fp32_bracket(const P &R, double sigma, int i, double b, double c
         const float y = (float)(mid / s);
         const double x = s * (double)y;                 // the point actually evaluated
         if (!(x > l && x < r)) break;
-        const float T = secular_sum_f32(R, sh, sl, sc, i, y, lane);
-        const double F = (b - x) + c * rcp(x) - K * (double)T;
-        if (F > 0.0) l = x;
+        const float Tf = secular_sum_f32(R, T, sh, sl, sc, skip, y);
+        const double phi = g64(x) - K * (double)Tf;
+        if ((phi > 0.0) == (dir > 0)) l = x;
         else r = x;
     }
     // widen by the bracket width and check both ends in FP64
     const double w = r - l;
     const double L = fmax(left, l - w), Rr = fmin(right, r + w);
-    if (L > left && !(pick_inverse_f64(R, sigma, i, b, c, L, lane) > 0.0)) return false;
-    if (Rr < right && !(pick_inverse_f64(R, sigma, i, b, c, Rr, lane) <= 0.0)) return false;
+    if (L > left) {
+        const double fl = f64(L);
+        if (fl == 0.0 || (fl > 0.0) != (dir > 0)) return false;
+    }
+    if (Rr < right) {
+        const double fr = f64(Rr);
+        if (fr != 0.0 && (fr > 0.0) == (dir > 0)) return false;
+    }
     left = L;
     right = Rr;
     return true;
 }
 
+// ---------------------------------------------------------------------------
 // Algorithm 2 + 3 for the shift pole i on `side`, then lambda = sigma + 1/nu.
-template <class P>
-__device__ EigResult solve_shifted(const P &R, int i, int side, const SolveOpts &o, int lane) {
+// ---------------------------------------------------------------------------
+template <class P, class Team>
+__device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
+                                   const SolveOpts &o) {
     EigResult res;
+    res.flags = 0;
     const double sigma = R.pole(i);
     const double zi = R.zabs(i);
     const double wz = 1.0 / zi;         // w_zeta
     const double c = wz * wz;           // 1/zeta_i^2
-    const PassA A = pass_a(R, sigma, i, wz, lane);
+    const PassA A = pass_a(R, T, sigma, i, wz);
     // b = (P - Q) / zeta_i^2 in double-double (Theorem 6), rounded once
     const dd num = dd_add(A.P, dd_neg(A.Q));
     const double b = dd_div(num, two_prod(zi, zi)).hi;
@@ -292,19 +380,19 @@ __device__ EigResult solve_shifted(const P &R, int i, int side, const SolveOpts 
         right = fmin(A.pmin, 0.0);
         left = fmin(fmin(A.lo, -wz), b - norm1);
     }
+    auto F64 = [&](double x) {
+        const double S = secular_sum(R, T, sigma, i, x);
+        return (b - x) - c * (S - rcp(x));
+    };
     if (o.precision == 1 && R.has_f32()) {
-        // FP32 opening bracket on a power-of-two rescaled copy (x = s y), then
-        // an FP64 check of both ends; on failure keep the Gershgorin bracket.
-        res.flags = 0;
-        if (!fp32_bracket(R, sigma, i, b, c, left, right, lane)) res.flags = 64;
-    } else {
-        res.flags = 0;
+        // F = (b - x) + c/x - c S(x),  c S(x) = (c s / zs) T(y)
+        auto G = [&](double x) { return (b - x) + c * rcp(x); };
+        if (!fp32_bracket(R, T, sigma, i, c, +1, G, F64, left, right)) res.flags |= 64;
     }
     int it = 0;
     double mid = 0.5 * (left + right);
     while (right - left > TWO_EPS * fabs(mid) && it < o.max_iter) {
-        const double S = secular_sum(R, sigma, i, mid, lane);
-        const double F = (b - mid) - c * (S - rcp(mid));
+        const double F = F64(mid);
         if (F > 0.0) left = mid;
         else right = mid;
         mid = 0.5 * (left + right);
@@ -328,24 +416,25 @@ __device__ EigResult solve_shifted(const P &R, int i, int side, const SolveOpts 
 // phi(x) = 1 + rho (S(x) - 1/x) with S over all poles.  The eigenvalue of A
 // closest to the shift on the side sign(rho) gives the extreme zero nu of
 // phi on that side; lambda = shift + 1/nu.
-template <class P>
-__device__ EigResult solve_dpr1_shift(const P &R, double shift, const SolveOpts &o, int lane) {
+template <class P, class Team>
+__device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
+                                      const SolveOpts &o) {
     EigResult res;
     res.sigma = shift;
     res.pole = -1;
     res.b = NAN;
     res.flags = 0;
-    const PassA A = pass_a(R, shift, -1, 1.0, lane);
-    const dd T = dd_add(A.P, dd_neg(A.Q));   // a - z^T (D - shift)^{-1} z = -T
-    res.Kb = (A.P.hi + A.Q.hi) / fabs(T.hi);
-    if (T.hi == 0.0) {                       // numerically singular: lambda = shift
+    const PassA A = pass_a(R, T, shift, -1, 1.0);
+    const dd Tn = dd_add(A.P, dd_neg(A.Q));   // a - z^T (D - shift)^{-1} z = -Tn
+    res.Kb = (A.P.hi + A.Q.hi) / fabs(Tn.hi);
+    if (Tn.hi == 0.0) {                       // numerically singular: lambda = shift
         res.mu = 0.0;
         res.lam = shift;
         res.iters = 0;
         res.flags = 32;
         return res;
     }
-    const double rho = -1.0 / T.hi;
+    const double rho = -1.0 / Tn.hi;
     const double usq = A.usq + 1.0;          // ||u||^2
     double left, right;
     if (rho > 0.0) {
@@ -355,14 +444,23 @@ __device__ EigResult solve_dpr1_shift(const P &R, double shift, const SolveOpts 
         right = fmin(A.pmin, 0.0);
         left = fma(rho, usq, right);
     }
+    // rho > 0: phi increases through the zero (phi < 0 below it); rho < 0: phi > 0 below
+    const int dir = rho > 0.0 ? -1 : +1;
+    auto PHI = [&](double x) {
+        const double S = secular_sum(R, T, shift, -1, x);
+        return fma(rho, S - rcp(x), 1.0);
+    };
+    if (o.precision == 1 && R.has_f32()) {
+        // phi = 1 - rho/x + rho S(x),  rho S(x) = (rho s / zs) T(y), so K_over_s = -rho
+        auto G = [&](double x) { return fma(-rho, rcp(x), 1.0); };
+        if (!fp32_bracket(R, T, shift, -1, -rho, dir, G, PHI, left, right)) res.flags |= 64;
+    }
     int it = 0;
     double mid = 0.5 * (left + right);
     while (right - left > TWO_EPS * fabs(mid) && it < o.max_iter) {
-        const double S = secular_sum(R, shift, -1, mid, lane);
-        const double phi = fma(rho, S - rcp(mid), 1.0);
-        // rho > 0: phi increases through the zero; rho < 0: it decreases
-        if ((phi > 0.0) == (rho > 0.0)) right = mid;
-        else left = mid;
+        const double phi = PHI(mid);
+        if ((phi > 0.0) == (dir > 0)) left = mid;
+        else right = mid;
         mid = 0.5 * (left + right);
         ++it;
     }
@@ -370,7 +468,7 @@ __device__ EigResult solve_dpr1_shift(const P &R, double shift, const SolveOpts 
     res.mu = 1.0 / nu;
     res.lam = shift + res.mu;
     res.iters = it;
-    res.flags = (it >= o.max_iter) ? 16 : 0;
+    res.flags |= (it >= o.max_iter) ? 16 : 0;
     return res;
 }
 
