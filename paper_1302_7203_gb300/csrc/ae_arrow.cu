@@ -425,21 +425,28 @@ __global__ void __launch_bounds__(256) k_vectors(int n, const double *__restrict
                 if (out.dg_flags) out.dg_flags[pos] = S.es_flags[k];
             }
             if (!col) continue;
-            // x_r = z_r / ((d_r - sigma) - mu) for every input row, x_{n-1} = -1;
-            // the norm is summed in sorted order so that it does not depend on
-            // the order of the input rows
+            // x_r = z_r / ((d_r - sigma) - mu) for every input row, x_{n-1} = -1.
+            // Pass 1 stores x in the column and sums x^2 in sorted order (so the
+            // norm does not depend on the order of the input rows); pass 2
+            // scales the column in place.
             double s = 0.0;
             for (int q = lane; q < n1; q += 32) {
                 const int r = S.perm[q];
                 const double zr = z[r];
                 const double x = zr == 0.0 ? 0.0 : zr * rcp((d[r] - sig) - mu);
+                col[r] = x;
                 s = fma(x, x, s);
             }
             s = warp_sum(s) + 1.0;
-            double scale = 1.0, inv;
             if (isfinite(s)) {
-                inv = 1.0 / sqrt(s);
-            } else {
+                const double inv = 1.0 / sqrt(s);
+                __syncwarp();
+                for (int r = lane; r < n1; r += 32) col[r] *= inv;
+                if (lane == 0) col[n1] = -inv;
+                continue;
+            }
+            double scale = 1.0, inv;
+            {
                 // rescale by the largest component to avoid overflow
                 double xm = 1.0;
                 for (int r = lane; r < n1; r += 32) {

@@ -323,20 +323,27 @@ __device__ bool fp32_bracket(const P &R, const Team &T, double shift, int skip, 
     if (!isfinite(sh)) return false;
     const float sc = (float)scd;
     const double K = K_over_s * s / R.zs;
+    // All terms of T have one sign on the searched side, so |T| bounds the sum
+    // of their magnitudes; an FP32 sum of m terms is then good to about
+    // (6 + sqrt(m)) 2^-24 |T|.  A decision whose |Phi| is below that is not
+    // trusted: the FP32 phase stops there.
+    const double tol32 = (6.0 + sqrt((double)R.m)) * 0x1p-24;
     double l = left, r = right;
     for (int it = 0; it < 80; ++it) {
         const double mid = 0.5 * (l + r);
-        if (r - l <= 0x1p-20 * fabs(mid)) break;
+        if (r - l <= 0x1p-21 * fabs(mid)) break;
         const float y = (float)(mid / s);
         const double x = s * (double)y;                 // the point actually evaluated
         if (!(x > l && x < r)) break;
         const float Tf = secular_sum_f32(R, T, sh, sl, sc, skip, y);
-        const double phi = g64(x) - K * (double)Tf;
+        const double KT = K * (double)Tf;
+        const double phi = g64(x) - KT;
+        if (!(fabs(phi) > tol32 * fabs(KT))) break;
         if ((phi > 0.0) == (dir > 0)) l = x;
         else r = x;
     }
-    // widen by the bracket width and check both ends in FP64
-    const double w = r - l;
+    // a small margin, then check both ends in FP64
+    const double w = 0.0625 * (r - l);
     const double L = fmax(left, l - w), Rr = fmin(right, r + w);
     if (L > left) {
         const double fl = f64(L);
