@@ -77,11 +77,8 @@ struct CtaTeam {
         for (int w = 1; w < NW; ++w) r += red[w];
         return r;
     }
-    __device__ __forceinline__ float sumf(float v) const {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-        return (float)sum((double)v);
-    }
+    // (sum() reduces within the warp itself: pass the per-thread value)
+    __device__ __forceinline__ float sumf(float v) const { return (float)sum((double)v); }
     __device__ __forceinline__ dd sum(dd v) const {
         v = warp_sum_dd(v);
         __syncthreads();
@@ -305,10 +302,12 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
 // ---------------------------------------------------------------------------
 // Narrow [left, right] (which holds the zero of a function Phi) with FP32
 // bisection, then verify the new ends in FP64.  Phi(x) = G(x) - K T(y), x = s y,
-// where G is the FP64 part (shift, b or 1, the 1/x term) and T the FP32 sum,
+// where G is the FP64 part (shift, b, the 1/x term) and T the FP32 sum,
 // K = K_over_s * s / zs.  `dir` = +1 when Phi > 0 below the zero, -1 when
-// above.  Returns false (bracket unchanged) when the FP32 data cannot
-// represent the problem or the FP64 check of an end fails.
+// above.  Each end is checked with one FP64 evaluation; an end that fails is
+// moved out by 16x its distance (twice at most) and otherwise left where it
+// was.  Returns false when the FP32 data cannot represent the problem or an
+// end had to be given up.
 template <class P, class Team, class G64, class F64>
 __device__ bool fp32_bracket(const P &R, const Team &T, double shift, int skip, double K_over_s,
                              int dir, G64 g64, F64 f64, double &left, double &right) {
@@ -323,11 +322,6 @@ __device__ bool fp32_bracket(const P &R, const Team &T, double shift, int skip, 
     if (!isfinite(sh)) return false;
     const float sc = (float)scd;
     const double K = K_over_s * s / R.zs;
-    // All terms of T have one sign on the searched side, so |T| bounds the sum
-    // of their magnitudes; an FP32 sum of m terms is then good to about
-    // (6 + sqrt(m)) 2^-24 |T|.  A decision whose |Phi| is below that is not
-    // trusted: the FP32 phase stops there.
-    const double tol32 = (6.0 + sqrt((double)R.m)) * 0x1p-24;
     double l = left, r = right;
     for (int it = 0; it < 80; ++it) {
         const double mid = 0.5 * (l + r);
@@ -338,24 +332,39 @@ __device__ bool fp32_bracket(const P &R, const Team &T, double shift, int skip, 
         const float Tf = secular_sum_f32(R, T, sh, sl, sc, skip, y);
         const double KT = K * (double)Tf;
         const double phi = g64(x) - KT;
-        if (!(fabs(phi) > tol32 * fabs(KT))) break;
+        if (!(fabs(phi) > 0x1p-24 * fabs(KT))) break;   // below FP32 resolution
         if ((phi > 0.0) == (dir > 0)) l = x;
         else r = x;
     }
-    // a small margin, then check both ends in FP64
-    const double w = 0.0625 * (r - l);
-    const double L = fmax(left, l - w), Rr = fmin(right, r + w);
-    if (L > left) {
-        const double fl = f64(L);
-        if (fl == 0.0 || (fl > 0.0) != (dir > 0)) return false;
+    const double w = r - l;
+    bool ok = true;
+    // left end: Phi must say "below the zero"
+    if (l > left) {
+        double off = w, L = left;
+        bool good = false;
+        for (int t = 0; t < 3 && !good; ++t, off *= 16.0) {
+            L = fmax(left, l - off);
+            if (L == left) { good = true; break; }
+            const double fl = f64(L);
+            good = fl != 0.0 && ((fl > 0.0) == (dir > 0));
+        }
+        if (good) left = L;
+        else ok = false;
     }
-    if (Rr < right) {
-        const double fr = f64(Rr);
-        if (fr != 0.0 && (fr > 0.0) == (dir > 0)) return false;
+    // right end: Phi must not say "below the zero"
+    if (r < right) {
+        double off = w, Rr = right;
+        bool good = false;
+        for (int t = 0; t < 3 && !good; ++t, off *= 16.0) {
+            Rr = fmin(right, r + off);
+            if (Rr == right) { good = true; break; }
+            const double fr = f64(Rr);
+            good = fr == 0.0 || ((fr > 0.0) != (dir > 0));
+        }
+        if (good) right = Rr;
+        else ok = false;
     }
-    left = L;
-    right = Rr;
-    return true;
+    return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -457,11 +466,9 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
         const double S = secular_sum(R, T, shift, -1, x);
         return fma(rho, S - rcp(x), 1.0);
     };
-    if (o.precision == 1 && R.has_f32()) {
-        // phi = 1 - rho/x + rho S(x),  rho S(x) = (rho s / zs) T(y), so K_over_s = -rho
-        auto G = [&](double x) { return fma(-rho, rcp(x), 1.0); };
-        if (!fp32_bracket(R, T, shift, -1, -rho, dir, G, PHI, left, right)) res.flags |= 64;
-    }
+    // (no FP32 opening here: with a shift next to lambda, nu ~ 1/(lambda - shift)
+    // is far outside what a power-of-two rescaled FP32 copy can represent, and
+    // these solves are a few per cent of all eigenpairs)
     int it = 0;
     double mid = 0.5 * (left + right);
     while (right - left > TWO_EPS * fabs(mid) && it < o.max_iter) {
