@@ -145,6 +145,56 @@ int arrow_eig(int n, const double *d, const double *z, double alpha,
               const ae_opts *opts, ae_info *info, const ae_diag *diag, void *stream);
 
 /*
+ * dpr1_eig -- all eigenpairs of the diagonal-plus-rank-one matrix
+ *     M = diag(d) + rho u u^T                                  (Sec. 6.3)
+ * of order n, through the paper's reduction to the arrowhead A = L^{-1} M L:
+ * after ordering d_1 > ... > d_n (and folding as below), A has poles
+ * d_1..d_{n-1}, spikes zeta_j = u_j sqrt(rho (d_j - d_n)) and corner
+ * d_n + rho u^T u, the last two in double-double.  rho < 0 is solved as
+ * -M = -diag(d) + |rho| u u^T.  The eigenvalue in (d_n, d_{n-1}) is re-solved
+ * from (A - d_n I)^{-1} (Remark 2(b)'s DPR1 inverse) when it is nearer d_n,
+ * so that lambda - d_n keeps its relative accuracy.
+ *
+ *  n       matrix order, n >= 1                                        (arg 1)
+ *  d, u    device, n doubles each, any order and sign; u_r = +-0 deflates
+ *          (d_r, e_r); exactly equal d fold like arrow_eig's equal poles (2, 3)
+ *  rho     the rank-one weight; rho = 0 returns sorted d and unit vectors (4)
+ *  lambda  device, n doubles out, descending                            (5)
+ *  Q       device, ldq*n doubles out or NULL: column k is the unit eigenvector
+ *          q ~ (diag(d) - lambda_k I)^{-1} u with a positive factor; deflated
+ *          columns as in arrow_eig (unit vectors, rotation vectors of runs) (6)
+ *  ldq     >= n                                                         (7)
+ *  opts, info, diag, stream: as arrow_eig                      (args 8-11)
+ */
+int dpr1_eig(int n, const double *d, const double *u, double rho, double *lambda, double *Q,
+             int ldq, const ae_opts *opts, ae_info *info, const ae_diag *diag, void *stream);
+
+/*
+ * tri_arrow_svd -- singular value decomposition B = U diag(sigma) V^T of the
+ * upper triangular arrowhead
+ *     B = [diag(d) z; 0 alpha]                                 (Sec. 6.2)
+ * of order n (d, z have n-1 entries), through the arrowhead B^T B with poles
+ * d_j^2, spikes d_j z_j and corner alpha^2 + z^T z (both in double-double);
+ * shifted differences to a pole are (d_j - d_i)(d_j + d_i).  sigma = sqrt(lambda),
+ * v the eigenvector of B^T B, u_j = sigma v_j / d_j, u_n = alpha v_n / sigma.
+ *
+ *  n       order, n >= 1                                               (arg 1)
+ *  d       device, n-1 doubles, each > 0 (any order); a d_r <= 0 is reported as
+ *          AE_ERR_INPUT (with info) -- flip row r of B to make it positive (2)
+ *  z       device, n-1 doubles; z_r = 0 deflates (d_r, e_r, e_r)            (3)
+ *  alpha   the corner, nonzero                                          (4)
+ *  sigma   device, n doubles out, descending                            (5)
+ *  U, ldu  device, ldu*n doubles out or NULL: left singular vectors (6, 7)
+ *  V, ldv  device, ldv*n doubles out or NULL (required when U is given):
+ *          right singular vectors, last component negative (x_n = -1 of
+ *          Eq. Aeigenvec applied to B^T B)                            (8, 9)
+ *  opts, info, diag, stream: as arrow_eig (diag refers to B^T B)  (args 10-13)
+ */
+int tri_arrow_svd(int n, const double *d, const double *z, double alpha, double *sigma,
+                  double *U, int ldu, double *V, int ldv, const ae_opts *opts, ae_info *info,
+                  const ae_diag *diag, void *stream);
+
+/*
  * arrow_eig_host -- arrow_eig on HOST buffers: copies d and z to the device,
  * solves, and copies lambda (and V, shift, mu when non-NULL) back, all on
  * `stream`, then synchronises.  Host buffers should be pinned for full
@@ -165,7 +215,7 @@ int arrow_eig_host(int n, const double *d_host, const double *z_host, double alp
  * Arguments, outputs and return codes are those of arrow_eig (opts->profile is
  * ignored).  The solve's scratch lives in one static device array of
  * AE_NOALLOC_SCRATCH_BYTES (4 MiB) that every GPU loading the library holds
- * until the process exits; n is limited to what fits, n <= 25537 (larger n
+ * until the process exits; n is limited to what fits, n <= 21376 (larger n
  * returns AE_ERR_TOO_LARGE without touching the GPU).  The call issues no
  * cudaMalloc/cudaFree and no allocating library routine.
  *  - Its first call on a device looks up the array's device address

@@ -29,7 +29,7 @@ FLAG_CAPPED, FLAG_SINGULAR, FLAG_FP32_FALLBACK = 16, 32, 64
 
 # every symbol include/arrowhead.h declares
 EXPORTED = ["ae_default_opts", "ae_status_string", "ae_last_cuda_error", "arrow_eig",
-            "arrow_eig_host", "arrow_eig_noalloc", "ae_debug_rcp"]
+            "dpr1_eig", "tri_arrow_svd", "arrow_eig_host", "arrow_eig_noalloc", "ae_debug_rcp"]
 AE_ERR_TOO_LARGE = 1004
 
 
@@ -87,6 +87,12 @@ def lib():
         L.arrow_eig_host.argtypes = [I, P, P, D, P, P, P, P, ctypes.POINTER(AeOpts),
                                      ctypes.POINTER(AeInfo), P]
         L.arrow_eig_host.restype = I
+        L.dpr1_eig.argtypes = [I, P, P, D, P, P, I, ctypes.POINTER(AeOpts),
+                               ctypes.POINTER(AeInfo), ctypes.POINTER(AeDiag), P]
+        L.dpr1_eig.restype = I
+        L.tri_arrow_svd.argtypes = [I, P, P, D, P, P, I, P, I, ctypes.POINTER(AeOpts),
+                                    ctypes.POINTER(AeInfo), ctypes.POINTER(AeDiag), P]
+        L.tri_arrow_svd.restype = I
         L.arrow_eig_noalloc.argtypes = L.arrow_eig.argtypes
         L.arrow_eig_noalloc.restype = I
         L.ae_debug_rcp.argtypes = [I, P, P, P]
@@ -182,6 +188,87 @@ def arrow_eig(d, z, alpha, *, vectors=True, want_shift=False, opts=None, info=Fa
     return res
 
 
+def _diag_arrays(n, dev):
+    import torch
+    return {"b": torch.empty(n, dtype=torch.float64, device=dev),
+            "Kb": torch.empty(n, dtype=torch.float64, device=dev),
+            "Knu": torch.empty(n, dtype=torch.float64, device=dev),
+            "iters": torch.empty(n, dtype=torch.int32, device=dev),
+            "flags": torch.empty(n, dtype=torch.int32, device=dev)}
+
+
+def dpr1_eig(d, u, rho, *, vectors=True, opts=None, info=False, diag=False, stream=None,
+             out=None):
+    """Eigen-decomposition of diag(d) + rho u u^T (float64 CUDA tensors, length n).
+
+    Returns ``lam`` (descending), ``Q`` (columns ``Q[:, k]``) when ``vectors``,
+    ``info`` and ``diag`` when requested."""
+    import torch
+    dev = d.device
+    n = int(d.numel())
+    out = dict(out or {})
+    lam = out.get("lam")
+    if lam is None:
+        lam = torch.empty(n, dtype=torch.float64, device=dev)
+    Q = out.get("Q") if vectors else None
+    if vectors and Q is None:
+        Q = torch.empty((n, n), dtype=torch.float64, device=dev)
+    o = opts if opts is not None else default_opts()
+    inf = AeInfo() if info else None
+    dgt = _diag_arrays(n, dev) if diag else {}
+    dg = AeDiag(*(t.data_ptr() for t in dgt.values())) if diag else None
+    st = lib().dpr1_eig(n, _ptr(d), _ptr(u), float(rho), _ptr(lam), _ptr(Q), n,
+                        ctypes.byref(o), ctypes.byref(inf) if inf is not None else None,
+                        ctypes.byref(dg) if dg is not None else None, _stream_handle(stream))
+    _check("dpr1_eig", st)
+    res = {"lam": lam}
+    if vectors:
+        res["Q"] = Q.t()
+    if info:
+        res["info"] = inf.as_dict()
+    if diag:
+        res["diag"] = dgt
+    return res
+
+
+def tri_arrow_svd(d, z, alpha, *, vectors=True, opts=None, info=False, diag=False,
+                  stream=None, out=None):
+    """SVD of [diag(d) z; 0 alpha] (d > 0, length n-1 float64 CUDA tensors).
+
+    Returns ``s`` (descending), ``U`` and ``V`` (columns) when ``vectors``."""
+    import torch
+    dev = d.device
+    n = int(d.numel()) + 1
+    out = dict(out or {})
+    s = out.get("s")
+    if s is None:
+        s = torch.empty(n, dtype=torch.float64, device=dev)
+    U = out.get("U") if vectors else None
+    V = out.get("V") if vectors else None
+    if vectors and U is None:
+        U = torch.empty((n, n), dtype=torch.float64, device=dev)
+    if vectors and V is None:
+        V = torch.empty((n, n), dtype=torch.float64, device=dev)
+    o = opts if opts is not None else default_opts()
+    inf = AeInfo() if info else None
+    dgt = _diag_arrays(n, dev) if diag else {}
+    dg = AeDiag(*(t.data_ptr() for t in dgt.values())) if diag else None
+    st = lib().tri_arrow_svd(n, _ptr(d), _ptr(z), float(alpha), _ptr(s), _ptr(U), n, _ptr(V),
+                             n, ctypes.byref(o), ctypes.byref(inf) if inf is not None else None,
+                             ctypes.byref(dg) if dg is not None else None,
+                             _stream_handle(stream))
+    _check("tri_arrow_svd", st)
+    res = {"s": s}
+    if vectors:
+        res["U"] = U.t()
+        res["V"] = V.t()
+    if info:
+        res["info"] = inf.as_dict()
+    if diag:
+        res["diag"] = dgt
+    return res
+
+
 def arrow_eig_host(d, z, alpha, *, vectors=True, want_shift=False, opts=None, stream=None,
                    out=None):
     """arrow_eig on host arrays (numpy or pinned torch CPU tensors).
@@ -230,7 +317,7 @@ def exported_symbols(path=LIB_PATH):
     return [s for s in EXPORTED if hasattr(L, s)]
 
 
-__all__ = ["arrow_eig", "arrow_eig_host", "debug_rcp", "default_opts", "lib", "AeOpts",
+__all__ = ["arrow_eig", "dpr1_eig", "tri_arrow_svd", "arrow_eig_host", "debug_rcp", "default_opts", "lib", "AeOpts",
            "AeInfo", "AeDiag", "AeError", "exported_symbols", "EXPORTED"]
 
 _ = np  # numpy is used by callers passing host arrays

@@ -103,15 +103,11 @@ const char *ae_status_string(int status) {
 
 const char *ae_last_cuda_error(void) { return g_err; }
 
-int arrow_eig(int n, const double *d, const double *z, double alpha, double *lambda,
-              double *V, int ldv, double *shift, double *mu, const ae_opts *opts,
-              ae_info *info, const ae_diag *diag, void *stream) {
-    if (n < 1) return -1;
-    if (n > 1 && !d) return -2;
-    if (n > 1 && !z) return -3;
-    if (!isfinite(alpha)) return -4;
-    if (!lambda) return -5;
-    if (V && ldv < n) return -7;
+// Shared by arrow_eig, dpr1_eig and tri_arrow_svd: scratch, launch, optional
+// synchronising summary.
+static int solve_common(ae::Kind kind, int n, const double *d, const double *z, double alpha,
+                        double rho, const ae::Outputs &out, const ae_opts *opts, ae_info *info,
+                        void *stream) {
     ae::RunOpts ro;
     if (resolve_opts(opts, ro)) return -10;
     cudaStream_t st = (cudaStream_t)stream;
@@ -125,19 +121,8 @@ int arrow_eig(int n, const double *d, const double *z, double alpha, double *lam
     cudaError_t e = cudaMallocAsync(&base, ae::arrow_scratch_bytes(n), st);
     if (e != cudaSuccess) return cuda_fail(e);
     ae::Scratch S = ae::carve_scratch(base, n);
-    ae::Outputs out;
-    out.lambda = lambda;
-    out.V = V;
-    out.ldv = ldv;
-    out.shift = shift;
-    out.mu = mu;
-    out.dg_b = diag ? diag->b : nullptr;
-    out.dg_Kb = diag ? diag->Kb : nullptr;
-    out.dg_Knu = diag ? diag->Knu : nullptr;
-    out.dg_iters = diag ? diag->iters : nullptr;
-    out.dg_flags = diag ? diag->flags : nullptr;
     int status = AE_OK;
-    e = ae::launch_arrow(n, d, z, alpha, out, ro, S, st);
+    e = ae::launch_solve(kind, n, d, z, alpha, rho, out, ro, S, st);
     if (e != cudaSuccess) status = cuda_fail(e);
     if (info && status == AE_OK) {
         int cnt[ae::C_COUNT];
@@ -175,6 +160,65 @@ int arrow_eig(int n, const double *d, const double *z, double alpha, double *lam
     e = cudaFreeAsync(base, st);
     if (e != cudaSuccess && status == AE_OK) status = cuda_fail(e);
     return status;
+}
+
+static ae::Outputs make_outputs(double *lambda, double *V, int ldv, double *U, int ldu,
+                                double *shift, double *mu, const ae_diag *diag) {
+    ae::Outputs out;
+    out.lambda = lambda;
+    out.V = V;
+    out.ldv = ldv;
+    out.U = U;
+    out.ldu = ldu;
+    out.shift = shift;
+    out.mu = mu;
+    out.dg_b = diag ? diag->b : nullptr;
+    out.dg_Kb = diag ? diag->Kb : nullptr;
+    out.dg_Knu = diag ? diag->Knu : nullptr;
+    out.dg_iters = diag ? diag->iters : nullptr;
+    out.dg_flags = diag ? diag->flags : nullptr;
+    return out;
+}
+
+int arrow_eig(int n, const double *d, const double *z, double alpha, double *lambda,
+              double *V, int ldv, double *shift, double *mu, const ae_opts *opts,
+              ae_info *info, const ae_diag *diag, void *stream) {
+    if (n < 1) return -1;
+    if (n > 1 && !d) return -2;
+    if (n > 1 && !z) return -3;
+    if (!isfinite(alpha)) return -4;
+    if (!lambda) return -5;
+    if (V && ldv < n) return -7;
+    const ae::Outputs out = make_outputs(lambda, V, ldv, nullptr, 0, shift, mu, diag);
+    return solve_common(ae::KIND_ARROW, n, d, z, alpha, 0.0, out, opts, info, stream);
+}
+
+int dpr1_eig(int n, const double *d, const double *u, double rho, double *lambda, double *Q,
+             int ldq, const ae_opts *opts, ae_info *info, const ae_diag *diag, void *stream) {
+    if (n < 1) return -1;
+    if (!d) return -2;
+    if (!u) return -3;
+    if (!isfinite(rho)) return -4;
+    if (!lambda) return -5;
+    if (Q && ldq < n) return -7;
+    const ae::Outputs out = make_outputs(lambda, Q, ldq, nullptr, 0, nullptr, nullptr, diag);
+    // rho = 0 is D itself: every row deflates (the spikes are scaled by rho)
+    return solve_common(ae::KIND_DPR1, n, d, u, 0.0, rho, out, opts, info, stream);
+}
+
+int tri_arrow_svd(int n, const double *d, const double *z, double alpha, double *sigma,
+                  double *U, int ldu, double *V, int ldv, const ae_opts *opts, ae_info *info,
+                  const ae_diag *diag, void *stream) {
+    if (n < 1) return -1;
+    if (n > 1 && !d) return -2;
+    if (n > 1 && !z) return -3;
+    if (!isfinite(alpha) || alpha == 0.0) return -4;
+    if (!sigma) return -5;
+    if (U && ldu < n) return -7;
+    if (V && ldv < n) return -9;
+    if (U && !V) return -8;
+    const ae::Outputs out = make_outputs(sigma, V, ldv, U, ldu, nullptr, nullptr, diag);
+    return solve_common(ae::KIND_TSVD, n, d, z, alpha, 0.0, out, opts, info, stream);
 }
 
 int arrow_eig_host(int n, const double *d_host, const double *z_host, double alpha,

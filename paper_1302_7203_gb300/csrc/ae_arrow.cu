@@ -1,18 +1,24 @@
-// ae_arrow.cu -- the arrowhead eigen-solver pipeline on one stream.
+// ae_arrow.cu -- the eigen-solver pipeline on one stream, for the three
+// problem kinds that reduce to a real symmetric arrowhead:
+//   ARROW  A = [diag(d) z; z^T alpha]                       (Sec. 1)
+//   DPR1   M = diag(d) + rho u u^T, via A = L^{-1} M L        (Sec. 6.3)
+//   SVD    B = [diag(d) z; 0 alpha], via A = B^T B            (Sec. 6.2)
 //
-//   k_check     validity / ordering flags of the input            (Sec. 1)
-//   k_rank      stable descending order (ties: lower input row)   (Sec. 1, Eq. order)
-//   k_reduce    zero spikes deflated, equal poles folded, reduced
-//               poles compacted (single CTA, block scans)         (Sec. 1)
-//   k_eig       one warp per eigenpair: Algorithm 1 shift choice,
-//               Algorithm 2 inverse with b in double-double
-//               (Theorem 6), Algorithm 3 bisection, lambda = sigma + 1/nu
-//   k_fix_decide / k_fix_solve
-//               Theorem C1 quotient > 3 -> Remark 1; K_nu (Eq. K0) above
-//               the threshold -> Remark 2(a) other pole or 2(b) DPR1 shift
-//   k_place     output positions (merge with deflated values)
-//   k_vectors   one warp per column: v = x/||x||, x = [(D-lambda)^{-1} z; -1]
-//               (Eq. eigenvecAi / Algorithm 4), coalesced column writes
+//   k_check      validity / ordering flags; transformed keys and spikes
+//   k_rank       stable descending order (ties: lower input row)   (Eq. order)
+//   k_reduce     zero spikes deflated, equal poles folded, reduced poles
+//                compacted (single CTA, block scans)               (Sec. 1)
+//   k_post<K>    kind-specific arrowhead data (DPR1: spikes and corner of
+//                L^{-1} M L; SVD: exact (d_j z_j)^2 and alpha^2 + z^T z), FP32 copies
+//   k_eig<P>     one warp per eigenpair: Algorithm 1 shift, Algorithm 2 inverse
+//                with b in double-double (Theorem 6), Algorithm 3 bisection
+//   k_fix_decide / k_fix_solve<P>
+//                Theorem C1 quotient > 3 -> Remark 1; K_nu (Eq. K0) above the
+//                threshold -> Remark 2(a) other pole or 2(b) DPR1 shift; DPR1:
+//                the last eigenvalue is re-solved next to the last pole
+//   k_place      output positions (merge with deflated values)
+//   k_vectors<K> one warp per column: v = x/||x|| (Eq. eigenvecAi / Algorithm 4),
+//                DPR1 q ~ (D - lambda)^{-1} u, SVD right and left vectors
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -23,24 +29,38 @@
 namespace ae {
 
 // ---------------------------------------------------------------------------
-// input checks and ordering
+// input checks, transformed keys/spikes, ordering
 // ---------------------------------------------------------------------------
-__global__ void k_check(int n1, const double *__restrict__ d, const double *__restrict__ z,
-                        int *cnt) {
+// ARROW: key d, spike z.  DPR1: key sgn d (sgn = sign of rho), spike u.
+// SVD: key d (> 0 required), spike d z.
+__global__ void k_check(Kind kind, int n1, const double *__restrict__ d,
+                        const double *__restrict__ z, double sgn, Scratch S) {
     int flags = 0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n1; r += gridDim.x * blockDim.x) {
         const double dr = d[r], zr = z[r];
         if (!isfinite(dr) || !isfinite(zr)) flags |= CF_BAD;
-        if (zr == 0.0) flags |= CF_ZERO;
-        if (dr == 0.0) flags |= CF_ZEROPOLE;
-        if (r + 1 < n1 && !(dr > d[r + 1])) flags |= CF_UNSORTED;
+        double key = dr, spk = zr;
+        if (kind == KIND_DPR1) {
+            key = sgn * dr;
+            S.key[r] = key;
+        } else if (kind == KIND_TSVD) {
+            if (!(dr > 0.0)) flags |= CF_BAD;
+            spk = dr * zr;
+            S.spk[r] = spk;
+        }
+        if (spk == 0.0) flags |= CF_ZERO;
+        if (key == 0.0) flags |= CF_ZEROPOLE;
+        if (r + 1 < n1) {
+            const double kn = kind == KIND_DPR1 ? sgn * d[r + 1] : d[r + 1];
+            if (!(key > kn)) flags |= CF_UNSORTED;
+        }
     }
     flags = __reduce_or_sync(FULL, flags);
-    if ((threadIdx.x & 31) == 0 && flags) atomicOr(cnt + C_FLAGS, flags);
+    if ((threadIdx.x & 31) == 0 && flags) atomicOr(S.cnt + C_FLAGS, flags);
 }
 
 // perm[s] = input row at sorted position s (descending, ties by lower row)
-__global__ void k_rank(int n1, const double *__restrict__ d, const int *cnt, int *perm) {
+__global__ void k_rank(int n1, const double *__restrict__ key, const int *cnt, int *perm) {
     __shared__ double tile[1024];
     const bool sorted = !(cnt[C_FLAGS] & CF_UNSORTED);
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -50,12 +70,12 @@ __global__ void k_rank(int n1, const double *__restrict__ d, const int *cnt, int
     }
     // NaN compares as -inf here so that ranks always form a permutation (the
     // input is rejected later, but no index may leave its array meanwhile)
-    const double dr = r < n1 ? (isnan(d[r]) ? -INFINITY : d[r]) : 0.0;
+    const double dr = r < n1 ? (isnan(key[r]) ? -INFINITY : key[r]) : 0.0;
     int rank = 0;
     for (int base = 0; base < n1; base += 1024) {
         __syncthreads();
         for (int t = threadIdx.x; t < 1024; t += blockDim.x) {
-            const double v = base + t < n1 ? d[base + t] : 0.0;
+            const double v = base + t < n1 ? key[base + t] : 0.0;
             tile[t] = isnan(v) ? -INFINITY : v;
         }
         __syncthreads();
@@ -101,8 +121,8 @@ __device__ __forceinline__ int block_exscan(int v, int *warp_tot, int &total) {
 }
 
 // Reduction (single CTA of 1024 threads, loops over chunks of the sorted order).
-__global__ void __launch_bounds__(1024) k_reduce(int n1, const double *__restrict__ d,
-                                                 const double *__restrict__ z,
+__global__ void __launch_bounds__(1024) k_reduce(int n1, const double *__restrict__ key,
+                                                 const double *__restrict__ spk,
                                                  const int *__restrict__ perm, Scratch S) {
     __shared__ int wt[33];
     int carry_keep = 0, carry_defl = 0;
@@ -114,15 +134,15 @@ __global__ void __launch_bounds__(1024) k_reduce(int n1, const double *__restric
         bool zero = false, head = false;
         if (s < n1) {
             r = perm[s];
-            dr = d[r];
-            zr = z[r];
+            dr = key[r];
+            zr = spk[r];
             zero = (zr == 0.0);
             if (!zero) {
                 head = true;   // the first nonzero row of its run of equal poles
                 for (int q = s - 1; q >= 0; --q) {
                     const int rq = perm[q];
-                    if (d[rq] != dr) break;
-                    if (z[rq] != 0.0) { head = false; break; }
+                    if (key[rq] != dr) break;
+                    if (spk[rq] != 0.0) { head = false; break; }
                 }
             }
             keep = head ? 1 : 0;
@@ -138,12 +158,15 @@ __global__ void __launch_bounds__(1024) k_reduce(int n1, const double *__restric
                 double acc = fabs(zr);
                 for (int q = s + 1; q < n1; ++q) {
                     const int rq = perm[q];
-                    if (d[rq] != dr) break;
-                    acc = hypot(acc, z[rq]);
+                    if (key[rq] != dr) break;
+                    acc = hypot(acc, spk[rq]);
                 }
                 S.pd[jk] = dr;
+                S.pv[jk] = dr;
                 S.pz[jk] = acc;
-                S.pz2[jk] = acc * acc;
+                const double a2 = acc * acc;
+                S.pz2[jk] = a2;
+                S.pz2lo[jk] = fma(acc, acc, -a2);
                 S.prow[jk] = r;
                 S.kind[r] = 0;
             } else {
@@ -157,8 +180,8 @@ __global__ void __launch_bounds__(1024) k_reduce(int n1, const double *__restric
                     int q = s - 1;
                     for (; q >= 0; --q) {
                         const int rq = perm[q];
-                        if (d[rq] != dr) break;
-                        Rm1 = hypot(Rm1, z[rq]);
+                        if (key[rq] != dr) break;
+                        Rm1 = hypot(Rm1, spk[rq]);
                     }
                     S.run_s0[r] = q + 1;
                     S.run_R[2 * r] = Rm1;
@@ -173,29 +196,102 @@ __global__ void __launch_bounds__(1024) k_reduce(int n1, const double *__restric
         S.cnt[C_M] = carry_keep;
         S.cnt[C_ND] = carry_defl;
     }
-    // FP32 copies for the opening bracket, scaled by powers of two so that the
-    // largest |pole| and the largest spike^2 are O(1)
+}
+
+// block reductions for the single-CTA post kernel (blockDim = 1024)
+__device__ __forceinline__ double block_max(double v, double *sh) {
+    v = warp_max(v);
     __syncthreads();
-    __shared__ double red[2][32];
-    const int m = carry_keep;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = sh[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+    return r;
+}
+
+__device__ __forceinline__ dd block_sum_dd(dd v, double *sh) {
+    v = warp_sum_dd(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        sh[threadIdx.x >> 5] = v.hi;
+        sh[32 + (threadIdx.x >> 5)] = v.lo;
+    }
+    __syncthreads();
+    dd r = {sh[0], sh[32]};
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = dd_add(r, dd{sh[w], sh[32 + w]});
+    return r;
+}
+
+// Kind-specific arrowhead data after the reduction, then the FP32 copies
+// (single CTA of 1024 threads).
+template <Kind K>
+__global__ void __launch_bounds__(1024) k_post(int n1, const double *__restrict__ d,
+                                               const double *__restrict__ z, double alpha,
+                                               double rho_abs, Scratch S) {
+    __shared__ double sh[64];
+    int m = S.cnt[C_M];
+    dd al = {alpha, 0.0};
+    if (K == KIND_DPR1) {
+        // Sec. 6.3: the reduced DPR1 poles p_0 > ... > p_{m-1} with weights u'_j;
+        // the arrowhead L^{-1} M L has poles p_0..p_{m-2}, spikes
+        // zeta_j = u'_j sqrt(rho (p_j - p_{m-1})) and corner p_{m-1} + rho u'^T u'
+        // (after u <- sqrt(rho) u); zeta_j^2 and the corner in double-double.
+        dd uu = {0.0, 0.0};
+        for (int j = threadIdx.x; j < m; j += blockDim.x) uu = dd_add_same(uu, two_prod(S.pz[j], S.pz[j]));
+        uu = block_sum_dd(uu, sh);
+        const double plast = m > 0 ? S.pd[m - 1] : 0.0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < m - 1; j += blockDim.x) {
+            const dd z2 = dd_mul(dd_mul_d(two_prod(S.pz[j], S.pz[j]), rho_abs),
+                                 two_sum(S.pd[j], -plast));
+            S.pz2[j] = z2.hi;
+            S.pz2lo[j] = z2.lo;
+            S.pz[j] = dd_sqrt(z2).hi;
+        }
+        al = dd_add(dd{plast, 0.0}, dd_mul_d(uu, rho_abs));
+        if (threadIdx.x == 0) {
+            S.prm[P_PLAST] = plast;
+            S.cnt[C_M] = m - 1;      // arrowhead poles; m - 1 = -1: nothing to solve
+        }
+        m = m - 1;
+    } else if (K == KIND_TSVD) {
+        // Sec. 6.2: B^T B has poles d_j^2, spikes d_j z_j, corner alpha^2 + z^T z
+        // (the corner over all rows; runs of equal d keep their folded spike).
+        dd zz = {0.0, 0.0};
+        for (int r = threadIdx.x; r < n1; r += blockDim.x) zz = dd_add_same(zz, two_prod(z[r], z[r]));
+        zz = block_sum_dd(zz, sh);
+        al = dd_add(two_prod(alpha, alpha), zz);
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const double dj = S.pd[j];
+            S.pv[j] = dj * dj;
+            const int r = S.prow[j];
+            // a single-row pole: (d_j z_j)^2 exactly in double-double
+            const bool single = (j + 1 == m || S.pd[j + 1] != dj) &&
+                                S.pz[j] == fabs(S.spk[r]);
+            if (single) {
+                const dd dz = two_prod(dj, z[r]);
+                const dd z2 = dd_mul(dz, dz);
+                S.pz2[j] = z2.hi;
+                S.pz2lo[j] = z2.lo;
+            }
+        }
+        const int nd = S.cnt[C_ND];
+        for (int t = threadIdx.x; t < nd; t += blockDim.x) S.dval[t] = S.dval[t] * S.dval[t];
+    }
+    if (threadIdx.x == 0) {
+        S.prm[P_ALPHA_HI] = al.hi;
+        S.prm[P_ALPHA_LO] = al.lo;
+    }
+    // FP32 copies: keys and spike^2 scaled by powers of two so that the
+    // largest of each is O(1)
     double mxd = 0.0, mxz = 0.0;
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
         mxd = fmax(mxd, fabs(S.pd[j]));
         mxz = fmax(mxz, S.pz2[j]);
     }
-    mxd = warp_max(mxd);
-    mxz = warp_max(mxz);
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = mxd;
-        red[1][threadIdx.x >> 5] = mxz;
-    }
-    __syncthreads();
-    mxd = 0.0;
-    mxz = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        mxd = fmax(mxd, red[0][w]);
-        mxz = fmax(mxz, red[1][w]);
-    }
+    mxd = block_max(mxd, sh);
+    mxz = block_max(mxz, sh);
     const double ds = (mxd > 0.0 && isfinite(mxd)) ? ldexp(1.0, -ilogb(mxd)) : 1.0;
     const double zs = (mxz > 0.0 && isfinite(mxz)) ? ldexp(1.0, -ilogb(mxz)) : 1.0;
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
@@ -206,14 +302,37 @@ __global__ void __launch_bounds__(1024) k_reduce(int n1, const double *__restric
         S.pz2f[j] = (float)(S.pz2[j] * zs);
     }
     if (threadIdx.x == 0) {
-        S.fscale[0] = ds;
-        S.fscale[1] = zs;
+        S.prm[P_DS] = ds;
+        S.prm[P_ZS] = zs;
     }
 }
 
 // ---------------------------------------------------------------------------
 // eigenpairs
 // ---------------------------------------------------------------------------
+template <Kind K>
+struct PolesOf;
+template <>
+struct PolesOf<KIND_ARROW> {
+    using type = ArrowPoles;
+    __device__ static ArrowPoles make(const Scratch &S, int m) {
+        return {m,      S.pd,  S.pz,  S.pz2,          S.pz2lo,        S.prm[P_ALPHA_HI],
+                S.prm[P_ALPHA_LO], S.pdh, S.pdl,      S.pz2f,         S.prm[P_DS],
+                S.prm[P_ZS]};
+    }
+};
+template <>
+struct PolesOf<KIND_DPR1> : PolesOf<KIND_ARROW> {};
+template <>
+struct PolesOf<KIND_TSVD> {
+    using type = TsvdPoles;
+    __device__ static TsvdPoles make(const Scratch &S, int m) {
+        return {m,     S.pd,     S.pv,              S.pz,  S.pz2, S.pz2lo,
+                S.prm[P_ALPHA_HI], S.prm[P_ALPHA_LO], S.pdh, S.pdl, S.pz2f,
+                S.prm[P_DS],       S.prm[P_ZS]};
+    }
+};
+
 __device__ __forceinline__ void store_result(const Scratch &S, int k, const EigResult &r) {
     S.es_sigma[k] = r.sigma;
     S.es_mu[k] = r.mu;
@@ -234,12 +353,12 @@ __device__ __forceinline__ void record_stats(const Scratch &S, const EigResult &
     if (isfinite(r.Kb)) atomic_max_nonneg(S.cnt64 + C64_MAXKB, r.Kb);
 }
 
-__global__ void __launch_bounds__(256) k_eig(double alpha, Scratch S, SolveOpts o) {
+template <Kind K>
+__global__ void __launch_bounds__(256) k_eig(Scratch S, SolveOpts o) {
     const int lane = threadIdx.x & 31;
     const int m = S.cnt[C_M];
     const int ncomp = m + 1;
-    const ArrowPoles R = {m,       S.pd,   S.pz,   S.pz2,          alpha,
-                          S.pdh,   S.pdl,  S.pz2f, S.fscale[0],    S.fscale[1]};
+    const auto R = PolesOf<K>::make(S, m);
     for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(S.cnt + C_WORK, 1);
@@ -247,7 +366,8 @@ __global__ void __launch_bounds__(256) k_eig(double alpha, Scratch S, SolveOpts 
         if (k >= ncomp) break;
         EigResult res;
         if (m == 0) {
-            res = {alpha, 0.0, alpha, NAN, 0.0, -1, 0, 0};
+            const double a = S.prm[P_ALPHA_HI];
+            res = {a, S.prm[P_ALPHA_LO], a, NAN, 0.0, -1, 0, 0};
         } else {
             const WarpTeam T{lane};
             int i, side;
@@ -264,18 +384,26 @@ __global__ void __launch_bounds__(256) k_eig(double alpha, Scratch S, SolveOpts 
 }
 
 // Remedy decisions: one thread per eigenpair.
-__global__ void k_fix_decide(Scratch S, double knu_max) {
+__global__ void k_fix_decide(Kind kind, Scratch S, double knu_max) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int m = S.cnt[C_M];
-    if (k > m || m == 0) return;
+    if (k > m || m <= 0) return;
     const double lam = S.es_lam[k], sig = S.es_sigma[k], mu = S.es_mu[k];
     const int i = S.es_pole[k];
     const double q = (fabs(sig) + fabs(mu)) / fabs(lam);
     int remedy = 0;
     double knu = 1.0;
-    // Theorem C1 bounds the quotient by 3 except in the special cases (a)-(c);
-    // Remark 1 needs D nonsingular.
-    if (q > 3.0 && !(S.cnt[C_FLAGS] & CF_ZEROPOLE)) {
+    if (kind == KIND_DPR1 && k == m &&
+        fabs(lam - S.prm[P_PLAST]) < fabs(mu)) {
+        // DPR1: the last eigenvalue lies between the last arrowhead pole and
+        // the DPR1's last pole p_last, which is not a pole of the arrowhead; when
+        // it is nearer p_last, re-solve from (A - p_last I)^{-1} so that
+        // lambda - p_last (and the vector's last component) keep relative accuracy.
+        S.es_fixshift[k] = S.prm[P_PLAST];
+        remedy = AE_FLAG_DPR1SHIFT;
+    } else if (q > 3.0 && !(S.cnt[C_FLAGS] & CF_ZEROPOLE)) {
+        // Theorem C1 bounds the quotient by 3 except in the special cases
+        // (a)-(c); Remark 1 needs D nonsingular.
         remedy = AE_FLAG_NEARZERO;
     } else if (i >= 0) {
         // K_nu = |mu| / min(|mu|, |mu_o|), mu_o from the eigenvalue on the other
@@ -290,7 +418,7 @@ __global__ void k_fix_decide(Scratch S, double knu_max) {
             const int io = mu > 0.0 ? i - 1 : i + 1;
             const int kn2 = mu > 0.0 ? k - 1 : k + 1;
             if (io >= 0 && io < m) {
-                const double po = S.pd[io];
+                const double po = S.pv[io];
                 const double mu2 = lam - po;
                 double k2 = 1.0;
                 if (kn2 >= 0 && kn2 <= m) {
@@ -305,8 +433,8 @@ __global__ void k_fix_decide(Scratch S, double knu_max) {
             if (!remedy) {
                 // Remark 2(b): shift near lambda, inside its interval, not a pole
                 double sh = lam;
-                const double lo = k < m ? S.pd[k] : -INFINITY;
-                const double hi = k > 0 ? S.pd[k - 1] : INFINITY;
+                const double lo = k < m ? S.pv[k] : -INFINITY;
+                const double hi = k > 0 ? S.pv[k - 1] : INFINITY;
                 if (!(sh > lo)) sh = nextafter(lo, INFINITY);
                 if (!(sh < hi)) sh = nextafter(hi, -INFINITY);
                 S.es_fixshift[k] = sh;
@@ -327,13 +455,13 @@ __global__ void k_fix_decide(Scratch S, double knu_max) {
 
 // Remedy solves: one CTA (8 warps) per listed eigenpair, so that the few
 // eigenpairs that need one still fill the GPU.
-__global__ void __launch_bounds__(256) k_fix_solve(double alpha, Scratch S, SolveOpts o) {
+template <Kind K>
+__global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o) {
     __shared__ double red[16];
     __shared__ int ticket;
     const int m = S.cnt[C_M];
     const int nfix = S.cnt[C_NFIX];
-    const ArrowPoles R = {m,       S.pd,   S.pz,   S.pz2,          alpha,
-                          S.pdh,   S.pdl,  S.pz2f, S.fscale[0],    S.fscale[1]};
+    const auto R = PolesOf<K>::make(S, m);
     const CtaTeam<8> T{(int)threadIdx.x, red};
     for (;;) {
         __syncthreads();
@@ -354,7 +482,7 @@ __global__ void __launch_bounds__(256) k_fix_solve(double alpha, Scratch S, Solv
             res = solve_dpr1_shift(R, T, S.es_fixshift[k], o);
         }
         // the result must stay in the eigenvalue's interlacing interval
-        const double lo = k < m ? R.pole(k) : -INFINITY;
+        const double lo = k < m ? R.pole(k) : (K == KIND_DPR1 ? S.prm[P_PLAST] : -INFINITY);
         const double hi = k > 0 ? R.pole(k - 1) : INFINITY;
         const bool ok = (res.lam >= lo && res.lam <= hi) && isfinite(res.lam);
         if (threadIdx.x == 0) {
@@ -399,25 +527,64 @@ __global__ void k_place(Scratch S) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_vectors(int n, const double *__restrict__ d,
+// Helmert-type vector of a run-folded row:
+// (-s_q sum_{l<m} s_l e_l + R_{m-1}^2 e_q) / (R_{m-1} R_m) with the run's spikes s
+__device__ __forceinline__ void run_column(const Scratch &S, const double *spk, int row, int lane,
+                                           double *col, double sign) {
+    const double Rm1 = S.run_R[2 * row], Rm = S.run_R[2 * row + 1];
+    const double zq = spk[row];
+    const double den = Rm1 * Rm;
+    const int s0 = S.run_s0[row], s1 = S.spos[row];
+    for (int s = s0 + lane; s < s1; s += 32) {
+        const int rq = S.perm[s];
+        const double zl = spk[rq];
+        if (zl != 0.0) col[rq] = sign * (-(zq * zl) / den);
+    }
+    if (lane == 0) col[row] = sign * (Rm1 / Rm);
+}
+
+// One warp per output column.  `key`/`spk` are the transformed inputs the
+// reduction saw; z is the caller's spike array (SVD: z, for the left vectors).
+template <Kind K>
+__global__ void __launch_bounds__(256) k_vectors(int n, int n1, const double *__restrict__ key,
+                                                 const double *__restrict__ spk,
                                                  const double *__restrict__ z, double alpha,
-                                                 Scratch S, Outputs out) {
+                                                 double sgn, Scratch S, Outputs out) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int n1 = n - 1;
     const int m = S.cnt[C_M], nd = S.cnt[C_ND];
     const int ncomp = m + 1;
+    const bool last_row = K != KIND_DPR1;     // arrowhead rows have the x_n = -1 entry
     for (int item = warp; item < ncomp + nd; item += nwarps) {
-        const int pos = S.pos[item];
+        int pos = S.pos[item];
+        if (K == KIND_DPR1 && sgn < 0.0) pos = n - 1 - pos;   // -M's order reversed
         double *col = out.V ? out.V + (size_t)pos * out.ldv : nullptr;
+        double *ucol = (K == KIND_TSVD && out.U) ? out.U + (size_t)pos * out.ldu : nullptr;
         if (item < ncomp) {
             const int k = item;
             const double sig = S.es_sigma[k], mu = S.es_mu[k];
+            const int pi = S.es_pole[k];
+            double value = S.es_lam[k];
+            double sv = 0.0;   // SVD: singular value
+            if (K == KIND_TSVD) {
+                // lambda = d_i^2 + mu (pole shift) or sigma + mu, in double-double
+                dd l2;
+                if (pi >= 0) {
+                    const double di = S.pd[pi];
+                    l2 = dd_add(two_prod(di, di), dd{mu, 0.0});
+                } else {
+                    l2 = two_sum(sig, mu);
+                }
+                sv = dd_sqrt(l2).hi;
+                value = sv;
+            } else if (K == KIND_DPR1) {
+                value = sgn * value;
+            }
             if (lane == 0) {
-                out.lambda[pos] = S.es_lam[k];
-                if (out.shift) out.shift[pos] = sig;
-                if (out.mu) out.mu[pos] = mu;
+                out.lambda[pos] = value;
+                if (out.shift) out.shift[pos] = K == KIND_DPR1 ? sgn * sig : sig;
+                if (out.mu) out.mu[pos] = K == KIND_DPR1 ? sgn * mu : mu;
                 if (out.dg_b) out.dg_b[pos] = S.es_b[k];
                 if (out.dg_Kb) out.dg_Kb[pos] = S.es_Kb[k];
                 if (out.dg_Knu) out.dg_Knu[pos] = S.es_Knu[k];
@@ -425,58 +592,76 @@ __global__ void __launch_bounds__(256) k_vectors(int n, const double *__restrict
                 if (out.dg_flags) out.dg_flags[pos] = S.es_flags[k];
             }
             if (!col) continue;
-            // x_r = z_r / ((d_r - sigma) - mu) for every input row, x_{n-1} = -1.
+            // component of row r: spike_r / (shifted difference of row r - mu)
+            auto comp = [&](int r) {
+                const double sr = spk[r];
+                if (sr == 0.0) return 0.0;
+                double del;
+                if (K == KIND_TSVD) {
+                    const double dr = key[r];
+                    if (pi >= 0) {
+                        const double di = S.pd[pi];
+                        del = (dr - di) * (dr + di);
+                    } else {
+                        del = fma(dr, dr, -sig);
+                    }
+                } else {
+                    del = key[r] - sig;
+                }
+                return sr * rcp(del - mu);
+            };
             // Pass 1 stores x in the column and sums x^2 in sorted order (so the
             // norm does not depend on the order of the input rows); pass 2
-            // scales the column in place.
+            // scales in place.
             double s = 0.0;
             for (int q = lane; q < n1; q += 32) {
                 const int r = S.perm[q];
-                const double zr = z[r];
-                const double x = zr == 0.0 ? 0.0 : zr * rcp((d[r] - sig) - mu);
+                const double x = comp(r);
                 col[r] = x;
                 s = fma(x, x, s);
             }
-            s = warp_sum(s) + 1.0;
-            if (isfinite(s)) {
-                const double inv = 1.0 / sqrt(s);
-                __syncwarp();
-                for (int r = lane; r < n1; r += 32) col[r] *= inv;
-                if (lane == 0) col[n1] = -inv;
-                continue;
-            }
-            double scale = 1.0, inv;
-            {
-                // rescale by the largest component to avoid overflow
-                double xm = 1.0;
-                for (int r = lane; r < n1; r += 32) {
-                    const double zr = z[r];
-                    if (zr != 0.0) xm = fmax(xm, fabs(zr * rcp((d[r] - sig) - mu)));
-                }
+            s = warp_sum(s) + (last_row ? 1.0 : 0.0);
+            double inv, scale = 1.0;
+            bool stored = true;
+            if (isfinite(s) && s > 0x1p-960) {
+                inv = 1.0 / sqrt(s);
+            } else {
+                // rescale by the largest component to avoid overflow/underflow
+                stored = false;
+                double xm = last_row ? 1.0 : 0.0;
+                for (int r = lane; r < n1; r += 32) xm = fmax(xm, fabs(comp(r)));
                 xm = warp_max(xm);
                 scale = 1.0 / xm;
                 double s2 = 0.0;
                 for (int q = lane; q < n1; q += 32) {
-                    const int r = S.perm[q];
-                    const double zr = z[r];
-                    const double x = zr == 0.0 ? 0.0 : zr * rcp((d[r] - sig) - mu) * scale;
+                    const double x = comp(S.perm[q]) * scale;
                     s2 = fma(x, x, s2);
                 }
-                s2 = warp_sum(s2) + scale * scale;
+                s2 = warp_sum(s2) + (last_row ? scale * scale : 0.0);
                 inv = 1.0 / sqrt(s2);
             }
+            // DPR1 with rho < 0 solved -M: q ~ (D - lambda)^{-1} u needs a sign flip
+            const double vs = (K == KIND_DPR1 && sgn < 0.0) ? -1.0 : 1.0;
+            __syncwarp();
             for (int r = lane; r < n1; r += 32) {
-                const double zr = z[r];
-                const double x = zr == 0.0 ? 0.0 : zr * rcp((d[r] - sig) - mu) * scale;
-                col[r] = x * inv;
+                const double x = stored ? col[r] : comp(r) * scale;
+                const double v = vs * x * inv;
+                col[r] = v;
+                if (ucol) ucol[r] = sv * v / key[r];      // u_j = s v_j / d_j
             }
-            if (lane == 0) col[n1] = -scale * inv;
+            if (last_row && lane == 0) {
+                const double vn = -scale * inv;
+                col[n1] = vn;
+                if (ucol) ucol[n1] = alpha * vn / sv;    // u_n = alpha v_n / s
+            }
         } else {
             const int u = item - ncomp;
             const int row = S.drow[u];
+            const double kv = key[row];
+            const double value = K == KIND_TSVD ? kv : (K == KIND_DPR1 ? sgn * kv : kv);
             if (lane == 0) {
-                out.lambda[pos] = S.dval[u];
-                if (out.shift) out.shift[pos] = S.dval[u];
+                out.lambda[pos] = value;
+                if (out.shift) out.shift[pos] = value;
                 if (out.mu) out.mu[pos] = 0.0;
                 if (out.dg_b) out.dg_b[pos] = NAN;
                 if (out.dg_Kb) out.dg_Kb[pos] = 0.0;
@@ -490,18 +675,12 @@ __global__ void __launch_bounds__(256) k_vectors(int n, const double *__restrict
             if (S.kind[row] == 1) {
                 if (lane == 0) col[row] = 1.0;
             } else {
-                // m-th later member q_m of a run of equal poles:
-                // (-z_{q_m} sum_{l<m} z_{q_l} e_{q_l} + R_{m-1}^2 e_{q_m}) / (R_{m-1} R_m)
-                const double Rm1 = S.run_R[2 * row], Rm = S.run_R[2 * row + 1];
-                const double zq = z[row];
-                const double den = Rm1 * Rm;
-                const int s0 = S.run_s0[row], s1 = S.spos[row];
-                for (int s = s0 + lane; s < s1; s += 32) {
-                    const int rq = S.perm[s];
-                    const double zl = z[rq];
-                    if (zl != 0.0) col[rq] = -(zq * zl) / den;
-                }
-                if (lane == 0) col[row] = Rm1 / Rm;
+                run_column(S, spk, row, lane, col, 1.0);
+            }
+            if (ucol) {
+                // B v = d_r v for a deflated right vector (its last entry is 0)
+                __syncwarp();
+                for (int r = lane; r < n; r += 32) ucol[r] = col[r];
             }
         }
     }
@@ -513,23 +692,12 @@ __global__ void k_debug_rcp(int n, const double *x, double *y) {
 }
 
 // ---------------------------------------------------------------------------
-// host orchestration
+// scratch layout
 // ---------------------------------------------------------------------------
-static int sm_count() {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-        if (cached <= 0) cached = 1;
-    }
-    return cached;
-}
-
 // One layout routine serves both sizing and carving, so they cannot disagree:
 // every array starts on a 256-byte boundary.
 static size_t layout(uintptr_t base, int n, Scratch *S) {
-    const size_t n1 = n > 1 ? (size_t)n - 1 : 1;
+    const size_t n1 = n > 1 ? (size_t)n : 1;     // rows: n - 1 (arrowhead) or n (DPR1)
     const size_t nn = (size_t)n;
     uintptr_t p = (base + 255) & ~(uintptr_t)255;
     const uintptr_t start = base;
@@ -541,18 +709,22 @@ static size_t layout(uintptr_t base, int n, Scratch *S) {
     Scratch T;
     T.cnt = (int *)take(sizeof(int) * C_COUNT);
     T.cnt64 = (unsigned long long *)take(sizeof(unsigned long long) * C64_COUNT);
+    T.prm = (double *)take(sizeof(double) * P_COUNT);
     T.perm = (int *)take(sizeof(int) * n1);
     T.spos = (int *)take(sizeof(int) * n1);
     T.kind = (int *)take(sizeof(int) * n1);
     T.run_s0 = (int *)take(sizeof(int) * n1);
     T.run_R = (double *)take(sizeof(double) * 2 * n1);
+    T.key = (double *)take(sizeof(double) * n1);
+    T.spk = (double *)take(sizeof(double) * n1);
     T.pd = (double *)take(sizeof(double) * n1);
     T.pz = (double *)take(sizeof(double) * n1);
     T.pz2 = (double *)take(sizeof(double) * n1);
+    T.pz2lo = (double *)take(sizeof(double) * n1);
+    T.pv = (double *)take(sizeof(double) * n1);
     T.pdh = (float *)take(sizeof(float) * n1);
     T.pdl = (float *)take(sizeof(float) * n1);
     T.pz2f = (float *)take(sizeof(float) * n1);
-    T.fscale = (double *)take(sizeof(double) * 2);
     T.prow = (int *)take(sizeof(int) * n1);
     T.drow = (int *)take(sizeof(int) * n1);
     T.dval = (double *)take(sizeof(double) * n1);
@@ -582,40 +754,91 @@ Scratch carve_scratch(void *base, int n) {
     return S;
 }
 
-// Issue the whole solve on `st`.  Scratch must hold arrow_scratch_bytes(n).
-cudaError_t launch_arrow(int n, const double *d, const double *z, double alpha,
-                         const Outputs &out, const RunOpts &ro, Scratch S, cudaStream_t st) {
-    const int n1 = n - 1;
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+static int sm_count() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+        if (cached <= 0) cached = 1;
+    }
+    return cached;
+}
+
+template <Kind K>
+static void launch_eig_kernels(int n, Scratch S, const SolveOpts &so, const RunOpts &ro,
+                               cudaStream_t st) {
+    const int sms = sm_count();
+    int grid = (n + 7) / 8;
+    grid = grid < sms * 8 ? grid : sms * 8;
+    if (ro.ev[1]) cudaEventRecord(ro.ev[1], st);
+    k_eig<K><<<grid, 256, 0, st>>>(S, so);
+    if (ro.ev[2]) cudaEventRecord(ro.ev[2], st);
+    if (ro.fixup) {
+        k_fix_decide<<<(n + 255) / 256, 256, 0, st>>>(K, S, ro.knu_max);
+        const int fgrid = n < sms * 4 ? n : sms * 4;
+        k_fix_solve<K><<<fgrid, 256, 0, st>>>(S, so);
+    }
+    if (ro.ev[3]) cudaEventRecord(ro.ev[3], st);
+}
+
+cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, double alpha,
+                         double rho, const Outputs &out, const RunOpts &ro, Scratch S,
+                         cudaStream_t st) {
+    const int n1 = kind == KIND_DPR1 ? n : n - 1;
+    const double sgn = (kind == KIND_DPR1 && rho < 0.0) ? -1.0 : 1.0;
+    const double *key = (kind == KIND_DPR1 && sgn < 0.0) ? S.key : d;
+    const bool rho0 = kind == KIND_DPR1 && rho == 0.0;   // M = D: every row deflates
+    const double *spk = (kind == KIND_TSVD || rho0) ? S.spk : z;
     cudaError_t e;
     e = cudaMemsetAsync(S.cnt, 0, sizeof(int) * C_COUNT, st);
     if (e) return e;
+    if (rho0 && n1 > 0) {
+        e = cudaMemsetAsync(S.spk, 0, sizeof(double) * n1, st);
+        if (e) return e;
+    }
     e = cudaMemsetAsync(S.cnt64, 0, sizeof(unsigned long long) * C64_COUNT, st);
     if (e) return e;
     const int sms = sm_count();
     if (ro.ev[0]) cudaEventRecord(ro.ev[0], st);
     if (n1 > 0) {
         const int g = (n1 + 255) / 256;
-        k_check<<<g, 256, 0, st>>>(n1, d, z, S.cnt);
-        k_rank<<<g, 256, 0, st>>>(n1, d, S.cnt, S.perm);
+        k_check<<<g, 256, 0, st>>>(kind, n1, d, z, sgn, S);
+        k_rank<<<g, 256, 0, st>>>(n1, key, S.cnt, S.perm);
     }
-    k_reduce<<<1, 1024, 0, st>>>(n1, d, z, S.perm, S);
+    k_reduce<<<1, 1024, 0, st>>>(n1, key, spk, S.perm, S);
     SolveOpts so{ro.max_iter, ro.precision};
-    const int warps = n;   // upper bound on eigenpairs
-    int grid = (warps + 7) / 8;
-    grid = grid < sms * 8 ? grid : sms * 8;
-    if (ro.ev[1]) cudaEventRecord(ro.ev[1], st);
-    k_eig<<<grid, 256, 0, st>>>(alpha, S, so);
-    if (ro.ev[2]) cudaEventRecord(ro.ev[2], st);
-    if (ro.fixup) {
-        k_fix_decide<<<(n + 255) / 256, 256, 0, st>>>(S, ro.knu_max);
-        int fgrid = n < sms * 4 ? n : sms * 4;
-        k_fix_solve<<<fgrid, 256, 0, st>>>(alpha, S, so);
+    switch (kind) {
+        case KIND_ARROW:
+            k_post<KIND_ARROW><<<1, 1024, 0, st>>>(n1, d, z, alpha, 0.0, S);
+            launch_eig_kernels<KIND_ARROW>(n, S, so, ro, st);
+            break;
+        case KIND_DPR1:
+            k_post<KIND_DPR1><<<1, 1024, 0, st>>>(n1, d, z, alpha, fabs(rho), S);
+            launch_eig_kernels<KIND_DPR1>(n, S, so, ro, st);
+            break;
+        case KIND_TSVD:
+            k_post<KIND_TSVD><<<1, 1024, 0, st>>>(n1, d, z, alpha, 0.0, S);
+            launch_eig_kernels<KIND_TSVD>(n, S, so, ro, st);
+            break;
     }
-    if (ro.ev[3]) cudaEventRecord(ro.ev[3], st);
     k_place<<<(n + 255) / 256, 256, 0, st>>>(S);
     int vgrid = (n + 7) / 8;
     vgrid = vgrid < sms * 16 ? vgrid : sms * 16;
-    k_vectors<<<vgrid, 256, 0, st>>>(n, d, z, alpha, S, out);
+    switch (kind) {
+        case KIND_ARROW:
+            k_vectors<KIND_ARROW><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, alpha, sgn, S, out);
+            break;
+        case KIND_DPR1:
+            k_vectors<KIND_DPR1><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, alpha, sgn, S, out);
+            break;
+        case KIND_TSVD:
+            k_vectors<KIND_TSVD><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, alpha, sgn, S, out);
+            break;
+    }
     if (ro.ev[4]) cudaEventRecord(ro.ev[4], st);
     return cudaGetLastError();
 }

@@ -73,6 +73,25 @@ __device__ __forceinline__ dd dd_add_same(dd x, dd y) {
 
 __device__ __forceinline__ dd dd_neg(dd x) { return {-x.hi, -x.lo}; }
 
+__device__ __forceinline__ dd dd_mul(dd x, dd y) {
+    dd p = two_prod(x.hi, y.hi);
+    p.lo = fma(x.hi, y.lo, fma(x.lo, y.hi, p.lo));
+    return fast_two_sum(p.hi, p.lo);
+}
+
+__device__ __forceinline__ dd dd_mul_d(dd x, double b) {
+    dd p = two_prod(x.hi, b);
+    p.lo = fma(x.lo, b, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+
+__device__ __forceinline__ dd dd_sqrt(dd x) {
+    if (!(x.hi > 0.0)) return {0.0, 0.0};
+    const double s = sqrt(x.hi);
+    const dd r = dd_add(x, dd_neg(two_prod(s, s)));
+    return fast_two_sum(s, r.hi / (2.0 * s));
+}
+
 // x / y with two partial quotients; the FMA residual x.hi - q1 y.hi is
 // (nearly) exact because q1 is within an ulp of the quotient
 __device__ __forceinline__ dd dd_div(dd x, dd y) {

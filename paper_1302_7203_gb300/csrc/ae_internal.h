@@ -29,6 +29,19 @@ enum { C64_ITERS = 0, C64_MAXKB = 1, C64_MAXKNU = 2, C64_ITERS_FIX = 3, C64_COUN
 // k_check flag bits
 enum { CF_UNSORTED = 1, CF_ZERO = 2, CF_BAD = 4, CF_ZEROPOLE = 8 };
 
+// problem kinds sharing the pipeline
+enum Kind { KIND_ARROW = 0, KIND_DPR1 = 1, KIND_TSVD = 2 };
+
+// slots of the per-solve double parameters
+enum {
+    P_ALPHA_HI = 0,   // corner of the arrowhead solved (double-double)
+    P_ALPHA_LO = 1,
+    P_PLAST = 2,      // DPR1: the last reduced pole (not an arrowhead pole)
+    P_DS = 3,         // FP32 copies: pole scale
+    P_ZS = 4,         // FP32 copies: spike^2 scale
+    P_COUNT = 8
+};
+
 struct Scratch {
     int *cnt;
     unsigned long long *cnt64;
@@ -37,9 +50,12 @@ struct Scratch {
     int *kind;      // input row: 0 pole head, 1 zero spike, 2 folded into a run
     int *run_s0;    // folded row: sorted position where its run starts
     double *run_R;  // folded row: R_{m-1}, R_m
-    double *pd, *pz, *pz2;  // reduced poles / spikes / fl(spike^2)
-    float *pdh, *pdl, *pz2f;  // FP32 copies: pole*ds split hi+lo, spike^2*zs
-    double *fscale;           // ds, zs (powers of two)
+    double *key, *spk;      // transformed inputs (DPR1 with rho < 0: -d; SVD: d z)
+    double *pd, *pz, *pz2;  // reduced keys (poles; SVD: d_j) / spikes / fl(spike^2)
+    double *pz2lo;          // spike^2 = pz2 + pz2lo (double-double)
+    double *pv;             // pole values (SVD: fl(d_j^2); else = pd)
+    float *pdh, *pdl, *pz2f;  // FP32 copies: key*ds split hi+lo, spike^2*zs
+    double *prm;              // P_* parameters
     int *prow;      // reduced pole -> input row of its head
     int *drow;      // deflated rows in sorted order
     double *dval;   // their pole values
@@ -49,9 +65,11 @@ struct Scratch {
 };
 
 struct Outputs {
-    double *lambda;
-    double *V;
+    double *lambda;     // eigenvalues (SVD: singular values)
+    double *V;          // eigenvectors (DPR1: Q; SVD: right singular vectors)
     long long ldv;
+    double *U;          // SVD: left singular vectors
+    long long ldu;
     double *shift, *mu;
     double *dg_b, *dg_Kb, *dg_Knu;
     int *dg_iters, *dg_flags;
@@ -67,8 +85,16 @@ struct RunOpts {
 
 size_t arrow_scratch_bytes(int n);
 Scratch carve_scratch(void *base, int n);
-cudaError_t launch_arrow(int n, const double *d, const double *z, double alpha,
-                         const Outputs &out, const RunOpts &ro, Scratch S, cudaStream_t st);
+// Issue a whole solve on `st`.  ARROW: d, z have n-1 entries; DPR1: d, u (in z)
+// have n entries and rho is used; SVD: d, z have n-1 entries.
+cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, double alpha,
+                         double rho, const Outputs &out, const RunOpts &ro, Scratch S,
+                         cudaStream_t st);
+inline cudaError_t launch_arrow(int n, const double *d, const double *z, double alpha,
+                                const Outputs &out, const RunOpts &ro, Scratch S,
+                                cudaStream_t st) {
+    return launch_solve(KIND_ARROW, n, d, z, alpha, 0.0, out, ro, S, st);
+}
 cudaError_t launch_debug_rcp(int n, const double *x, double *y, cudaStream_t st);
 // remember a CUDA error for ae_last_cuda_error()
 void record_cuda_error(cudaError_t e);

@@ -84,6 +84,8 @@ extern "C" int arrow_eig_noalloc(int n, const double *d, const double *z, double
     out.lambda = lambda;
     out.V = V;
     out.ldv = ldv;
+    out.U = nullptr;
+    out.ldu = 0;
     out.shift = shift;
     out.mu = mu;
     out.dg_b = diag ? diag->b : nullptr;

@@ -121,8 +121,9 @@ struct ArrowPoles {
     int m;
     const double *__restrict__ pd;   // poles, strictly decreasing
     const double *__restrict__ pz;   // zeta_j > 0
-    const double *__restrict__ pz2;  // fl(zeta_j^2)
-    double alpha;
+    const double *__restrict__ pz2;  // zeta_j^2 = pz2 + pz2lo
+    const double *__restrict__ pz2lo;
+    double alpha, alpha_lo;          // corner (double-double)
     // FP32 copies for the opening bracket: poles split hi + lo after scaling
     // by ds, and zeta^2 scaled by zs (ds, zs powers of two); null when absent
     const float *__restrict__ pdh;
@@ -140,16 +141,81 @@ struct ArrowPoles {
     }
     __device__ __forceinline__ double z2(int j) const { return __ldg(pz2 + j); }
     __device__ __forceinline__ double zabs(int j) const { return __ldg(pz + j); }
-    __device__ __forceinline__ dd z2_dd(int j) const {
-        double z = __ldg(pz + j);
-        return two_prod(z, z);
+    __device__ __forceinline__ dd z2_dd(int j) const { return {__ldg(pz2 + j), __ldg(pz2lo + j)}; }
+    // a = alpha - shift, exact for a double alpha
+    __device__ __forceinline__ dd a_dd(double shift, int) const {
+        return dd_add(two_sum(alpha, -shift), dd{alpha_lo, 0.0});
     }
-    // a = alpha - shift, exact
-    __device__ __forceinline__ dd a_dd(double shift, int) const { return two_sum(alpha, -shift); }
-    // scaled shifted difference (p_j - shift) * ds in FP32 from the hi/lo split
+    // FP32: the shift split hi + lo after scaling, and the scaled difference
+    __device__ __forceinline__ void f32_shift(double shift, int, float &sh, float &sl) const {
+        const double ss = shift * ds;
+        sh = (float)ss;
+        sl = (float)(ss - (double)sh);
+    }
     __device__ __forceinline__ float shifted_f32(int j, float sh, float sl) const {
         return (__ldg(pdh + j) - sh) + (__ldg(pdl + j) - sl);
     }
+    __device__ __forceinline__ double f32_scale() const { return ds; }
+    __device__ __forceinline__ float z2f(int j) const { return __ldg(pz2f + j); }
+    __device__ __forceinline__ bool has_f32() const { return pdh != nullptr; }
+};
+
+// The arrowhead B^T B of the triangular arrowhead B = [D z; 0 alpha] (Sec. 6.2):
+// poles d_j^2, spikes d_j z_j, corner alpha^2 + z^T z.  Shifted differences to
+// a pole use the paper's (d_j - d_i)(d_j + d_i); to any other shift, one fused
+// d_j d_j - shift.
+struct TsvdPoles {
+    int m;
+    const double *__restrict__ pd;   // d_j > 0, strictly decreasing
+    const double *__restrict__ pv;   // fl(d_j^2)
+    const double *__restrict__ pz;   // |d_j z_j|
+    const double *__restrict__ pz2;  // (d_j z_j)^2 = pz2 + pz2lo
+    const double *__restrict__ pz2lo;
+    double alpha, alpha_lo;          // alpha^2 + z^T z (double-double)
+    const float *__restrict__ pdh;   // d_j * ds split hi + lo
+    const float *__restrict__ pdl;
+    const float *__restrict__ pz2f;
+    double ds, zs;
+
+    __device__ __forceinline__ double pole(int j) const { return __ldg(pv + j); }
+    __device__ __forceinline__ double shifted(int j, double shift, int i) const {
+        const double dj = __ldg(pd + j);
+        if (i >= 0) {
+            const double di = __ldg(pd + i);
+            return (dj - di) * (dj + di);
+        }
+        return fma(dj, dj, -shift);
+    }
+    __device__ __forceinline__ dd shifted_dd(int j, double shift, int i) const {
+        const double dj = __ldg(pd + j);
+        if (i >= 0) {
+            const double di = __ldg(pd + i);
+            return dd_mul(two_sum(dj, -di), two_sum(dj, di));
+        }
+        return dd_add(two_prod(dj, dj), dd{-shift, 0.0});
+    }
+    __device__ __forceinline__ double z2(int j) const { return __ldg(pz2 + j); }
+    __device__ __forceinline__ double zabs(int j) const { return __ldg(pz + j); }
+    __device__ __forceinline__ dd z2_dd(int j) const { return {__ldg(pz2 + j), __ldg(pz2lo + j)}; }
+    __device__ __forceinline__ dd a_dd(double shift, int i) const {
+        const dd al = {alpha, alpha_lo};
+        if (i >= 0) {
+            const double di = __ldg(pd + i);
+            return dd_add(al, dd_neg(two_prod(di, di)));
+        }
+        return dd_add(al, dd{-shift, 0.0});
+    }
+    // FP32 only for pole shifts: split d_i; differences (d_j - d_i)(d_j + d_i) ds^2
+    __device__ __forceinline__ void f32_shift(double, int i, float &sh, float &sl) const {
+        const double ss = __ldg(pd + (i >= 0 ? i : 0)) * ds;
+        sh = (float)ss;
+        sl = (float)(ss - (double)sh);
+    }
+    __device__ __forceinline__ float shifted_f32(int j, float sh, float sl) const {
+        const float h = __ldg(pdh + j), l = __ldg(pdl + j);
+        return ((h - sh) + (l - sl)) * ((h + sh) + (l + sl));
+    }
+    __device__ __forceinline__ double f32_scale() const { return ds * ds; }
     __device__ __forceinline__ float z2f(int j) const { return __ldg(pz2f + j); }
     __device__ __forceinline__ bool has_f32() const { return pdh != nullptr; }
 };
@@ -314,11 +380,10 @@ __device__ bool fp32_bracket(const P &R, const Team &T, double shift, int skip, 
     const double big = fmax(fabs(left), fabs(right));
     if (!(big > 0.0) || !isfinite(big)) return false;
     const double s = ldexp(1.0, ilogb(big));          // x = s y, |y| <= 2
-    const double scd = s / R.ds;                        // D_j = (p_j - shift) ds * scd
+    const double scd = s / R.f32_scale();               // D_j = scaled difference * scd
     if (!(scd > 0x1p-120 && scd < 0x1p120)) return false;
-    const double ss = shift * R.ds;
-    const float sh = (float)ss;
-    const float sl = (float)(ss - (double)sh);
+    float sh, sl;
+    R.f32_shift(shift, skip, sh, sl);
     if (!isfinite(sh)) return false;
     const float sc = (float)scd;
     const double K = K_over_s * s / R.zs;
