@@ -195,6 +195,59 @@ int tri_arrow_svd(int n, const double *d, const double *z, double alpha, double 
                   const ae_diag *diag, void *stream);
 
 /*
+ * Batched arrowheads: `count` independent instances of orders n_i >= 1, solved
+ * together -- each stage of the arrow_eig pipeline is one persistent launch
+ * over all instances (eigenpairs of every instance share one work queue and
+ * are solved by teams of W = 8, 16 or 32 lanes, W chosen per order bucket by
+ * ae_autotune and cached).  The method per instance is that of arrow_eig
+ * (Algorithms 1-3, Theorem 6, Remarks 1-2); the batching is this library's.
+ *
+ * Layout (all device arrays except n_off / v_off, which are HOST arrays of
+ * count + 1 int64 prefix sums):
+ *   n_off[i]       sum of n_j for j < i (n_off[0] = 0, n_off[count] = total)
+ *   d_all, z_all   instance i's n_i - 1 poles / spikes start at n_off[i] - i
+ *   alpha_all[i]   corner of instance i
+ *   lambda_all     instance i's eigenvalues (descending) start at n_off[i]
+ *   V_all          NULL, or instance i's n_i x n_i column-major eigenvectors
+ *                  (ld = n_i) start at v_off[i] (v_off NULL: packed, the prefix
+ *                  sums of n_i^2)
+ *   status_all     NULL, or per-instance AE_OK / AE_ERR_INPUT / AE_ERR_NOCONV
+ * Conventions per instance are those of arrow_eig.  Returns -k for argument k.
+ */
+typedef struct ae_batch ae_batch;
+
+/* One-shot batched solve on `stream` (synchronises before returning, since it
+   frees its scratch).  info, if given, sums the per-instance counters. */
+int arrow_eig_batched(int count, const long long *n_off, const long long *v_off,
+                      const double *d_all, const double *z_all, const double *alpha_all,
+                      double *lambda_all, double *V_all, int *status_all, const ae_opts *opts,
+                      ae_info *info, void *stream);
+
+/* A reusable plan for repeated solves of the same shapes and buffers: builds
+   the descriptor table and all scratch (cudaMalloc), and captures the whole
+   solve in a CUDA graph.  The plan keeps the buffer addresses: change their
+   contents, not the buffers, between runs.  Arguments as arrow_eig_batched
+   (plan is arg 1, count arg 2 ...). */
+int ae_batch_create(ae_batch **plan, int count, const long long *n_off,
+                    const long long *v_off, const double *d_all, const double *z_all,
+                    const double *alpha_all, double *lambda_all, double *V_all,
+                    int *status_all, const ae_opts *opts, void *stream);
+/* Replay the captured solve on `stream` (asynchronous). */
+int ae_batch_run(ae_batch *plan, void *stream);
+/* Counters of the last run, summed over instances (synchronises `stream`). */
+int ae_batch_info(ae_batch *plan, ae_info *info, void *stream);
+/* Free the plan (waits for the device). */
+void ae_batch_destroy(ae_batch *plan);
+
+/* Time team widths 8, 16, 32 on synthetic instances for order buckets
+   32..256 (larger buckets use 32) and store the fastest per bucket in the JSON
+   cache $AE_TUNE_CACHE (default ~/.cache/arrowhead_tune.json), keyed by the
+   device name and the library build.  Plans created afterwards use it. */
+int ae_autotune(int n_max, void *stream);
+/* The team width the batched solver uses for an instance of order n. */
+int ae_team_width(int n);
+
+/*
  * arrow_eig_host -- arrow_eig on HOST buffers: copies d and z to the device,
  * solves, and copies lambda (and V, shift, mu when non-NULL) back, all on
  * `stream`, then synchronises.  Host buffers should be pinned for full

@@ -29,7 +29,9 @@ FLAG_CAPPED, FLAG_SINGULAR, FLAG_FP32_FALLBACK = 16, 32, 64
 
 # every symbol include/arrowhead.h declares
 EXPORTED = ["ae_default_opts", "ae_status_string", "ae_last_cuda_error", "arrow_eig",
-            "dpr1_eig", "tri_arrow_svd", "arrow_eig_host", "arrow_eig_noalloc", "ae_debug_rcp"]
+            "dpr1_eig", "tri_arrow_svd", "arrow_eig_batched", "ae_batch_create",
+            "ae_batch_run", "ae_batch_info", "ae_batch_destroy", "ae_autotune",
+            "ae_team_width", "arrow_eig_host", "arrow_eig_noalloc", "ae_debug_rcp"]
 AE_ERR_TOO_LARGE = 1004
 
 
@@ -93,6 +95,23 @@ def lib():
         L.tri_arrow_svd.argtypes = [I, P, P, D, P, P, I, P, I, ctypes.POINTER(AeOpts),
                                     ctypes.POINTER(AeInfo), ctypes.POINTER(AeDiag), P]
         L.tri_arrow_svd.restype = I
+        LLP = ctypes.POINTER(ctypes.c_longlong)
+        L.arrow_eig_batched.argtypes = [I, LLP, LLP, P, P, P, P, P, P, ctypes.POINTER(AeOpts),
+                                        ctypes.POINTER(AeInfo), P]
+        L.arrow_eig_batched.restype = I
+        L.ae_batch_create.argtypes = [ctypes.POINTER(P), I, LLP, LLP, P, P, P, P, P, P,
+                                      ctypes.POINTER(AeOpts), P]
+        L.ae_batch_create.restype = I
+        L.ae_batch_run.argtypes = [P, P]
+        L.ae_batch_run.restype = I
+        L.ae_batch_info.argtypes = [P, ctypes.POINTER(AeInfo), P]
+        L.ae_batch_info.restype = I
+        L.ae_batch_destroy.argtypes = [P]
+        L.ae_batch_destroy.restype = None
+        L.ae_autotune.argtypes = [I, P]
+        L.ae_autotune.restype = I
+        L.ae_team_width.argtypes = [I]
+        L.ae_team_width.restype = I
         L.arrow_eig_noalloc.argtypes = L.arrow_eig.argtypes
         L.arrow_eig_noalloc.restype = I
         L.ae_debug_rcp.argtypes = [I, P, P, P]
@@ -269,6 +288,95 @@ def tri_arrow_svd(d, z, alpha, *, vectors=True, opts=None, info=False, diag=Fals
     return res
 
 
+class Batch:
+    """Packed device buffers for a batch of arrowheads and the C plan over them.
+
+    ``instances`` is a list of (d, z, alpha) (numpy, length n_i - 1).  The
+    inputs are uploaded once; ``run()`` replays the captured solve; results are
+    views into ``lam_all`` / ``V_all``.  ``graph=False`` uses the one-shot
+    arrow_eig_batched instead of a plan.
+    """
+
+    def __init__(self, instances, *, vectors=True, opts=None, graph=True, stream=None,
+                 device="cuda"):
+        import torch
+        self.count = len(instances)
+        ns = np.array([len(d) + 1 for d, _, _ in instances], dtype=np.int64)
+        self.n = ns
+        self.n_off = np.zeros(self.count + 1, dtype=np.int64)
+        np.cumsum(ns, out=self.n_off[1:])
+        self.v_off = np.zeros(self.count + 1, dtype=np.int64)
+        np.cumsum(ns * ns, out=self.v_off[1:])
+        cat = lambda k: np.concatenate([np.asarray(x[k], dtype=np.float64) for x in instances]) \
+            if self.n_off[-1] > self.count else np.zeros(1)
+        self.d_all = torch.as_tensor(cat(0), device=device)
+        self.z_all = torch.as_tensor(cat(1), device=device)
+        self.alpha_all = torch.as_tensor(np.array([x[2] for x in instances], dtype=np.float64),
+                                         device=device)
+        self.lam_all = torch.empty(int(self.n_off[-1]), dtype=torch.float64, device=device)
+        self.V_all = torch.empty(int(self.v_off[-1]), dtype=torch.float64, device=device) \
+            if vectors else None
+        self.status = torch.empty(self.count, dtype=torch.int32, device=device)
+        self.opts = opts if opts is not None else default_opts()
+        self.stream = stream
+        self.plan = None
+        if graph:
+            h = ctypes.c_void_p()
+            st = lib().ae_batch_create(ctypes.byref(h), self.count, self._ll(self.n_off),
+                                       self._ll(self.v_off), _ptr(self.d_all), _ptr(self.z_all),
+                                       _ptr(self.alpha_all), _ptr(self.lam_all), _ptr(self.V_all),
+                                       _ptr(self.status), ctypes.byref(self.opts),
+                                       _stream_handle(stream))
+            _check("ae_batch_create", st)
+            self.plan = h
+
+    @staticmethod
+    def _ll(a):
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+
+    def run(self, info=False):
+        inf = AeInfo() if info else None
+        if self.plan is not None:
+            _check("ae_batch_run", lib().ae_batch_run(self.plan, _stream_handle(self.stream)))
+            if info:
+                _check("ae_batch_info", lib().ae_batch_info(self.plan, ctypes.byref(inf),
+                                                            _stream_handle(self.stream)))
+        else:
+            st = lib().arrow_eig_batched(self.count, self._ll(self.n_off), self._ll(self.v_off),
+                                         _ptr(self.d_all), _ptr(self.z_all),
+                                         _ptr(self.alpha_all), _ptr(self.lam_all),
+                                         _ptr(self.V_all), _ptr(self.status),
+                                         ctypes.byref(self.opts),
+                                         ctypes.byref(inf) if inf is not None else None,
+                                         _stream_handle(self.stream))
+            _check("arrow_eig_batched", st)
+        return inf.as_dict() if info else None
+
+    def lam(self, i):
+        return self.lam_all[self.n_off[i]:self.n_off[i + 1]]
+
+    def V(self, i):
+        n = int(self.n[i])
+        return self.V_all[self.v_off[i]:self.v_off[i + 1]].view(n, n).t()
+
+    def close(self):
+        if self.plan is not None:
+            lib().ae_batch_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(n_max=4096, stream=None):
+    """Run the team-width tuner and store its choices in the JSON cache."""
+    _check("ae_autotune", lib().ae_autotune(int(n_max), _stream_handle(stream)))
+    return {b: lib().ae_team_width(b) for b in (32, 64, 128, 256, 512)}
+
+
 def arrow_eig_host(d, z, alpha, *, vectors=True, want_shift=False, opts=None, stream=None,
                    out=None):
     """arrow_eig on host arrays (numpy or pinned torch CPU tensors).
@@ -317,7 +425,8 @@ def exported_symbols(path=LIB_PATH):
     return [s for s in EXPORTED if hasattr(L, s)]
 
 
-__all__ = ["arrow_eig", "dpr1_eig", "tri_arrow_svd", "arrow_eig_host", "debug_rcp", "default_opts", "lib", "AeOpts",
+__all__ = ["arrow_eig", "dpr1_eig", "tri_arrow_svd", "Batch", "autotune", "arrow_eig_host",
+           "debug_rcp", "default_opts", "lib", "AeOpts",
            "AeInfo", "AeDiag", "AeError", "exported_symbols", "EXPORTED"]
 
 _ = np  # numpy is used by callers passing host arrays

@@ -24,7 +24,7 @@
 #include <stdint.h>
 
 #include "ae_internal.h"
-#include "ae_solver.cuh"
+#include "ae_pipeline.cuh"
 
 namespace ae {
 
@@ -91,366 +91,43 @@ __global__ void k_rank(int n1, const double *__restrict__ key, const int *cnt, i
     if (r < n1) perm[rank] = r;
 }
 
-// block-wide exclusive scan of one int per thread (blockDim = 1024)
-__device__ __forceinline__ int block_exscan(int v, int *warp_tot, int &total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int t = warp_tot[lane];
-        int u = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(FULL, u, o);
-            if (lane >= o) u += y;
-        }
-        warp_tot[lane] = u - t;       // exclusive prefix of warp totals
-        if (lane == 31) warp_tot[32] = u;
-    }
-    __syncthreads();
-    const int res = warp_tot[wid] + x - v;
-    total = warp_tot[32];
-    __syncthreads();
-    return res;
-}
-
-// Reduction (single CTA of 1024 threads, loops over chunks of the sorted order).
+// Reduction (single CTA of 1024 threads) and the kind-specific arrowhead data.
 __global__ void __launch_bounds__(1024) k_reduce(int n1, const double *__restrict__ key,
                                                  const double *__restrict__ spk,
                                                  const int *__restrict__ perm, Scratch S) {
-    __shared__ int wt[33];
-    int carry_keep = 0, carry_defl = 0;
-    for (int base = 0; base < n1; base += 1024) {
-        const int s = base + threadIdx.x;
-        int keep = 0, defl = 0;
-        int r = -1;
-        double dr = 0.0, zr = 0.0;
-        bool zero = false, head = false;
-        if (s < n1) {
-            r = perm[s];
-            dr = key[r];
-            zr = spk[r];
-            zero = (zr == 0.0);
-            if (!zero) {
-                head = true;   // the first nonzero row of its run of equal poles
-                for (int q = s - 1; q >= 0; --q) {
-                    const int rq = perm[q];
-                    if (key[rq] != dr) break;
-                    if (spk[rq] != 0.0) { head = false; break; }
-                }
-            }
-            keep = head ? 1 : 0;
-            defl = head ? 0 : 1;
-        }
-        int tk, td;
-        const int jk = block_exscan(keep, wt, tk) + carry_keep;
-        const int jd = block_exscan(defl, wt, td) + carry_defl;
-        if (s < n1) {
-            S.spos[r] = s;
-            if (head) {
-                // reduced spike: sqrt of the sum of squares over the run
-                double acc = fabs(zr);
-                for (int q = s + 1; q < n1; ++q) {
-                    const int rq = perm[q];
-                    if (key[rq] != dr) break;
-                    acc = hypot(acc, spk[rq]);
-                }
-                S.pd[jk] = dr;
-                S.pv[jk] = dr;
-                S.pz[jk] = acc;
-                const double a2 = acc * acc;
-                S.pz2[jk] = a2;
-                S.pz2lo[jk] = fma(acc, acc, -a2);
-                S.prow[jk] = r;
-                S.kind[r] = 0;
-            } else {
-                S.kind[r] = zero ? 1 : 2;
-                S.drow[jd] = r;
-                S.dval[jd] = dr;
-                if (!zero) {
-                    // Helmert-type vector data: R_{m-1} over earlier nonzero
-                    // members of the run, R_m including this row
-                    double Rm1 = 0.0;
-                    int q = s - 1;
-                    for (; q >= 0; --q) {
-                        const int rq = perm[q];
-                        if (key[rq] != dr) break;
-                        Rm1 = hypot(Rm1, spk[rq]);
-                    }
-                    S.run_s0[r] = q + 1;
-                    S.run_R[2 * r] = Rm1;
-                    S.run_R[2 * r + 1] = hypot(Rm1, zr);
-                }
-            }
-        }
-        carry_keep += tk;
-        carry_defl += td;
-    }
-    if (threadIdx.x == 0) {
-        S.cnt[C_M] = carry_keep;
-        S.cnt[C_ND] = carry_defl;
-    }
+    reduce_block(n1, key, spk, perm, S);
 }
 
-// block reductions for the single-CTA post kernel (blockDim = 1024)
-__device__ __forceinline__ double block_max(double v, double *sh) {
-    v = warp_max(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double r = sh[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
-    return r;
-}
-
-__device__ __forceinline__ dd block_sum_dd(dd v, double *sh) {
-    v = warp_sum_dd(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) {
-        sh[threadIdx.x >> 5] = v.hi;
-        sh[32 + (threadIdx.x >> 5)] = v.lo;
-    }
-    __syncthreads();
-    dd r = {sh[0], sh[32]};
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = dd_add(r, dd{sh[w], sh[32 + w]});
-    return r;
-}
-
-// Kind-specific arrowhead data after the reduction, then the FP32 copies
-// (single CTA of 1024 threads).
 template <Kind K>
 __global__ void __launch_bounds__(1024) k_post(int n1, const double *__restrict__ d,
                                                const double *__restrict__ z, double alpha,
                                                double rho_abs, Scratch S) {
-    __shared__ double sh[64];
-    int m = S.cnt[C_M];
-    dd al = {alpha, 0.0};
-    if (K == KIND_DPR1) {
-        // Sec. 6.3: the reduced DPR1 poles p_0 > ... > p_{m-1} with weights u'_j;
-        // the arrowhead L^{-1} M L has poles p_0..p_{m-2}, spikes
-        // zeta_j = u'_j sqrt(rho (p_j - p_{m-1})) and corner p_{m-1} + rho u'^T u'
-        // (after u <- sqrt(rho) u); zeta_j^2 and the corner in double-double.
-        dd uu = {0.0, 0.0};
-        for (int j = threadIdx.x; j < m; j += blockDim.x) uu = dd_add_same(uu, two_prod(S.pz[j], S.pz[j]));
-        uu = block_sum_dd(uu, sh);
-        const double plast = m > 0 ? S.pd[m - 1] : 0.0;
-        __syncthreads();
-        for (int j = threadIdx.x; j < m - 1; j += blockDim.x) {
-            const dd z2 = dd_mul(dd_mul_d(two_prod(S.pz[j], S.pz[j]), rho_abs),
-                                 two_sum(S.pd[j], -plast));
-            S.pz2[j] = z2.hi;
-            S.pz2lo[j] = z2.lo;
-            S.pz[j] = dd_sqrt(z2).hi;
-        }
-        al = dd_add(dd{plast, 0.0}, dd_mul_d(uu, rho_abs));
-        if (threadIdx.x == 0) {
-            S.prm[P_PLAST] = plast;
-            S.cnt[C_M] = m - 1;      // arrowhead poles; m - 1 = -1: nothing to solve
-        }
-        m = m - 1;
-    } else if (K == KIND_TSVD) {
-        // Sec. 6.2: B^T B has poles d_j^2, spikes d_j z_j, corner alpha^2 + z^T z
-        // (the corner over all rows; runs of equal d keep their folded spike).
-        dd zz = {0.0, 0.0};
-        for (int r = threadIdx.x; r < n1; r += blockDim.x) zz = dd_add_same(zz, two_prod(z[r], z[r]));
-        zz = block_sum_dd(zz, sh);
-        al = dd_add(two_prod(alpha, alpha), zz);
-        __syncthreads();
-        for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            const double dj = S.pd[j];
-            S.pv[j] = dj * dj;
-            const int r = S.prow[j];
-            // a single-row pole: (d_j z_j)^2 exactly in double-double
-            const bool single = (j + 1 == m || S.pd[j + 1] != dj) &&
-                                S.pz[j] == fabs(S.spk[r]);
-            if (single) {
-                const dd dz = two_prod(dj, z[r]);
-                const dd z2 = dd_mul(dz, dz);
-                S.pz2[j] = z2.hi;
-                S.pz2lo[j] = z2.lo;
-            }
-        }
-        const int nd = S.cnt[C_ND];
-        for (int t = threadIdx.x; t < nd; t += blockDim.x) S.dval[t] = S.dval[t] * S.dval[t];
-    }
-    if (threadIdx.x == 0) {
-        S.prm[P_ALPHA_HI] = al.hi;
-        S.prm[P_ALPHA_LO] = al.lo;
-    }
-    // FP32 copies: keys and spike^2 scaled by powers of two so that the
-    // largest of each is O(1)
-    double mxd = 0.0, mxz = 0.0;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        mxd = fmax(mxd, fabs(S.pd[j]));
-        mxz = fmax(mxz, S.pz2[j]);
-    }
-    mxd = block_max(mxd, sh);
-    mxz = block_max(mxz, sh);
-    const double ds = (mxd > 0.0 && isfinite(mxd)) ? ldexp(1.0, -ilogb(mxd)) : 1.0;
-    const double zs = (mxz > 0.0 && isfinite(mxz)) ? ldexp(1.0, -ilogb(mxz)) : 1.0;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        const double v = S.pd[j] * ds;
-        const float h = (float)v;
-        S.pdh[j] = h;
-        S.pdl[j] = (float)(v - (double)h);
-        S.pz2f[j] = (float)(S.pz2[j] * zs);
-    }
-    if (threadIdx.x == 0) {
-        S.prm[P_DS] = ds;
-        S.prm[P_ZS] = zs;
-    }
+    post_block<K>(n1, d, z, alpha, rho_abs, S);
 }
 
 // ---------------------------------------------------------------------------
 // eigenpairs
 // ---------------------------------------------------------------------------
 template <Kind K>
-struct PolesOf;
-template <>
-struct PolesOf<KIND_ARROW> {
-    using type = ArrowPoles;
-    __device__ static ArrowPoles make(const Scratch &S, int m) {
-        return {m,      S.pd,  S.pz,  S.pz2,          S.pz2lo,        S.prm[P_ALPHA_HI],
-                S.prm[P_ALPHA_LO], S.pdh, S.pdl,      S.pz2f,         S.prm[P_DS],
-                S.prm[P_ZS]};
-    }
-};
-template <>
-struct PolesOf<KIND_DPR1> : PolesOf<KIND_ARROW> {};
-template <>
-struct PolesOf<KIND_TSVD> {
-    using type = TsvdPoles;
-    __device__ static TsvdPoles make(const Scratch &S, int m) {
-        return {m,     S.pd,     S.pv,              S.pz,  S.pz2, S.pz2lo,
-                S.prm[P_ALPHA_HI], S.prm[P_ALPHA_LO], S.pdh, S.pdl, S.pz2f,
-                S.prm[P_DS],       S.prm[P_ZS]};
-    }
-};
-
-__device__ __forceinline__ void store_result(const Scratch &S, int k, const EigResult &r) {
-    S.es_sigma[k] = r.sigma;
-    S.es_mu[k] = r.mu;
-    S.es_lam[k] = r.lam;
-    S.es_b[k] = r.b;
-    S.es_Kb[k] = r.Kb;
-    S.es_pole[k] = r.pole;
-    S.es_iters[k] = r.iters;
-}
-
-__device__ __forceinline__ void record_stats(const Scratch &S, const EigResult &r,
-                                             bool fix = false) {
-    atomicAdd(S.cnt64 + C64_ITERS, (unsigned long long)r.iters);
-    if (fix) atomicAdd(S.cnt64 + C64_ITERS_FIX, (unsigned long long)r.iters);
-    atomicMax(S.cnt + C_MAXIT, r.iters);
-    if (r.flags & AE_FLAG_CAPPED) atomicAdd(S.cnt + C_CAPPED, 1);
-    if (r.flags & AE_FLAG_FP32_FALLBACK) atomicAdd(S.cnt + C_FP32FB, 1);
-    if (isfinite(r.Kb)) atomic_max_nonneg(S.cnt64 + C64_MAXKB, r.Kb);
-}
-
-template <Kind K>
 __global__ void __launch_bounds__(256) k_eig(Scratch S, SolveOpts o) {
     const int lane = threadIdx.x & 31;
     const int m = S.cnt[C_M];
     const int ncomp = m + 1;
     const auto R = PolesOf<K>::make(S, m);
+    const WarpTeam T{lane};
     for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(S.cnt + C_WORK, 1);
         k = __shfl_sync(FULL, k, 0);
         if (k >= ncomp) break;
-        EigResult res;
-        if (m == 0) {
-            const double a = S.prm[P_ALPHA_HI];
-            res = {a, S.prm[P_ALPHA_LO], a, NAN, 0.0, -1, 0, 0};
-        } else {
-            const WarpTeam T{lane};
-            int i, side;
-            select_shift(R, T, k, i, side);
-            res = solve_shifted(R, T, i, side, o);
-        }
-        if (lane == 0) {
-            store_result(S, k, res);
-            S.es_flags[k] = res.flags;
-            S.es_Knu[k] = 1.0;
-            record_stats(S, res);
-        }
+        eig_item<K>(R, T, S, k, o);
     }
 }
 
 // Remedy decisions: one thread per eigenpair.
 __global__ void k_fix_decide(Kind kind, Scratch S, double knu_max) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int m = S.cnt[C_M];
-    if (k > m || m <= 0) return;
-    const double lam = S.es_lam[k], sig = S.es_sigma[k], mu = S.es_mu[k];
-    const int i = S.es_pole[k];
-    const double q = (fabs(sig) + fabs(mu)) / fabs(lam);
-    int remedy = 0;
-    double knu = 1.0;
-    if (kind == KIND_DPR1 && k == m &&
-        fabs(lam - S.prm[P_PLAST]) < fabs(mu)) {
-        // DPR1: the last eigenvalue lies between the last arrowhead pole and
-        // the DPR1's last pole p_last, which is not a pole of the arrowhead; when
-        // it is nearer p_last, re-solve from (A - p_last I)^{-1} so that
-        // lambda - p_last (and the vector's last component) keep relative accuracy.
-        S.es_fixshift[k] = S.prm[P_PLAST];
-        remedy = AE_FLAG_DPR1SHIFT;
-    } else if (q > 3.0 && !(S.cnt[C_FLAGS] & CF_ZEROPOLE)) {
-        // Theorem C1 bounds the quotient by 3 except in the special cases
-        // (a)-(c); Remark 1 needs D nonsingular.
-        remedy = AE_FLAG_NEARZERO;
-    } else if (i >= 0) {
-        // K_nu = |mu| / min(|mu|, |mu_o|), mu_o from the eigenvalue on the other
-        // side of the shift pole
-        const int kn = mu > 0.0 ? k + 1 : k - 1;
-        if (kn >= 0 && kn <= m) {
-            const double muo = (S.es_sigma[kn] - sig) + S.es_mu[kn];
-            knu = fmax(1.0, fabs(mu) / fabs(muo));
-        }
-        if (knu > knu_max) {
-            // Remark 2(a): the other pole of lambda's interval, if its K_nu is small
-            const int io = mu > 0.0 ? i - 1 : i + 1;
-            const int kn2 = mu > 0.0 ? k - 1 : k + 1;
-            if (io >= 0 && io < m) {
-                const double po = S.pv[io];
-                const double mu2 = lam - po;
-                double k2 = 1.0;
-                if (kn2 >= 0 && kn2 <= m) {
-                    const double muo2 = (S.es_sigma[kn2] - po) + S.es_mu[kn2];
-                    k2 = fmax(1.0, fabs(mu2) / fabs(muo2));
-                }
-                if (k2 <= knu_max) {
-                    remedy = AE_FLAG_OTHERPOLE;
-                    S.es_fixpole[k] = io;
-                }
-            }
-            if (!remedy) {
-                // Remark 2(b): shift near lambda, inside its interval, not a pole
-                double sh = lam;
-                const double lo = k < m ? S.pv[k] : -INFINITY;
-                const double hi = k > 0 ? S.pv[k - 1] : INFINITY;
-                if (!(sh > lo)) sh = nextafter(lo, INFINITY);
-                if (!(sh < hi)) sh = nextafter(hi, -INFINITY);
-                S.es_fixshift[k] = sh;
-                remedy = AE_FLAG_DPR1SHIFT;
-            }
-        }
-    }
-    S.es_Knu[k] = knu;
-    atomic_max_nonneg(S.cnt64 + C64_MAXKNU, knu);
-    if (remedy) {
-        S.es_flags[k] |= remedy;
-        const int slot = atomicAdd(S.cnt + C_NFIX, 1);
-        S.fixlist[slot] = k;
-        atomicAdd(S.cnt + (remedy == AE_FLAG_NEARZERO ? C_NEARZERO
-                           : remedy == AE_FLAG_OTHERPOLE ? C_OTHERPOLE : C_DPR1), 1);
-    }
+    if (fix_decide_item(kind, S, k, knu_max)) S.fixlist[atomicAdd(S.cnt + C_NFIX, 1)] = k;
 }
 
 // Remedy solves: one CTA (8 warps) per listed eigenpair, so that the few
@@ -469,82 +146,15 @@ __global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o) {
         __syncthreads();
         const int w = ticket;
         if (w >= nfix) break;
-        const int k = S.fixlist[w];
-        const int f = S.es_flags[k];
-        EigResult res;
-        if (f & AE_FLAG_NEARZERO) {
-            res = solve_dpr1_shift(R, T, 0.0, o);
-        } else if (f & AE_FLAG_OTHERPOLE) {
-            const int io = S.es_fixpole[k];
-            const int side = io < S.es_pole[k] ? -1 : +1;   // other pole above -> lambda below it
-            res = solve_shifted(R, T, io, side, o);
-        } else {
-            res = solve_dpr1_shift(R, T, S.es_fixshift[k], o);
-        }
-        // the result must stay in the eigenvalue's interlacing interval
-        const double lo = k < m ? R.pole(k) : (K == KIND_DPR1 ? S.prm[P_PLAST] : -INFINITY);
-        const double hi = k > 0 ? R.pole(k - 1) : INFINITY;
-        const bool ok = (res.lam >= lo && res.lam <= hi) && isfinite(res.lam);
-        if (threadIdx.x == 0) {
-            if (ok) {
-                // b and K_b stay those of Algorithm 1's shift pole
-                res.b = S.es_b[k];
-                res.Kb = S.es_Kb[k];
-                store_result(S, k, res);
-                S.es_flags[k] = f | res.flags;
-                record_stats(S, res, true);
-            } else {
-                S.es_flags[k] = f & ~(AE_FLAG_NEARZERO | AE_FLAG_OTHERPOLE | AE_FLAG_DPR1SHIFT);
-            }
-        }
+        fix_solve_item<K>(R, T, S, S.fixlist[w], o);
     }
 }
 
 // ---------------------------------------------------------------------------
 // output placement and vectors
 // ---------------------------------------------------------------------------
-// number of entries of a non-increasing array that are >= x (or > x)
-__device__ __forceinline__ int count_ge(const double *a, int len, double x, bool strict) {
-    int lo = 0, hi = len;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const bool in = strict ? (a[mid] > x) : (a[mid] >= x);
-        if (in) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
+__global__ void k_place(Scratch S) { place_item(S, blockIdx.x * blockDim.x + threadIdx.x); }
 
-__global__ void k_place(Scratch S) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int m = S.cnt[C_M], nd = S.cnt[C_ND];
-    const int ncomp = m + 1;
-    if (t < ncomp) {
-        S.pos[t] = nd ? t + count_ge(S.dval, nd, S.es_lam[t], false) : t;
-    } else if (t < ncomp + nd) {
-        const int u = t - ncomp;
-        S.pos[t] = u + count_ge(S.es_lam, ncomp, S.dval[u], true);
-    }
-}
-
-// Helmert-type vector of a run-folded row:
-// (-s_q sum_{l<m} s_l e_l + R_{m-1}^2 e_q) / (R_{m-1} R_m) with the run's spikes s
-__device__ __forceinline__ void run_column(const Scratch &S, const double *spk, int row, int lane,
-                                           double *col, double sign) {
-    const double Rm1 = S.run_R[2 * row], Rm = S.run_R[2 * row + 1];
-    const double zq = spk[row];
-    const double den = Rm1 * Rm;
-    const int s0 = S.run_s0[row], s1 = S.spos[row];
-    for (int s = s0 + lane; s < s1; s += 32) {
-        const int rq = S.perm[s];
-        const double zl = spk[rq];
-        if (zl != 0.0) col[rq] = sign * (-(zq * zl) / den);
-    }
-    if (lane == 0) col[row] = sign * (Rm1 / Rm);
-}
-
-// One warp per output column.  `key`/`spk` are the transformed inputs the
-// reduction saw; z is the caller's spike array (SVD: z, for the left vectors).
 template <Kind K>
 __global__ void __launch_bounds__(256) k_vectors(int n, int n1, const double *__restrict__ key,
                                                  const double *__restrict__ spk,
@@ -553,137 +163,9 @@ __global__ void __launch_bounds__(256) k_vectors(int n, int n1, const double *__
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int m = S.cnt[C_M], nd = S.cnt[C_ND];
-    const int ncomp = m + 1;
-    const bool last_row = K != KIND_DPR1;     // arrowhead rows have the x_n = -1 entry
-    for (int item = warp; item < ncomp + nd; item += nwarps) {
-        int pos = S.pos[item];
-        if (K == KIND_DPR1 && sgn < 0.0) pos = n - 1 - pos;   // -M's order reversed
-        double *col = out.V ? out.V + (size_t)pos * out.ldv : nullptr;
-        double *ucol = (K == KIND_TSVD && out.U) ? out.U + (size_t)pos * out.ldu : nullptr;
-        if (item < ncomp) {
-            const int k = item;
-            const double sig = S.es_sigma[k], mu = S.es_mu[k];
-            const int pi = S.es_pole[k];
-            double value = S.es_lam[k];
-            double sv = 0.0;   // SVD: singular value
-            if (K == KIND_TSVD) {
-                // lambda = d_i^2 + mu (pole shift) or sigma + mu, in double-double
-                dd l2;
-                if (pi >= 0) {
-                    const double di = S.pd[pi];
-                    l2 = dd_add(two_prod(di, di), dd{mu, 0.0});
-                } else {
-                    l2 = two_sum(sig, mu);
-                }
-                sv = dd_sqrt(l2).hi;
-                value = sv;
-            } else if (K == KIND_DPR1) {
-                value = sgn * value;
-            }
-            if (lane == 0) {
-                out.lambda[pos] = value;
-                if (out.shift) out.shift[pos] = K == KIND_DPR1 ? sgn * sig : sig;
-                if (out.mu) out.mu[pos] = K == KIND_DPR1 ? sgn * mu : mu;
-                if (out.dg_b) out.dg_b[pos] = S.es_b[k];
-                if (out.dg_Kb) out.dg_Kb[pos] = S.es_Kb[k];
-                if (out.dg_Knu) out.dg_Knu[pos] = S.es_Knu[k];
-                if (out.dg_iters) out.dg_iters[pos] = S.es_iters[k];
-                if (out.dg_flags) out.dg_flags[pos] = S.es_flags[k];
-            }
-            if (!col) continue;
-            // component of row r: spike_r / (shifted difference of row r - mu)
-            auto comp = [&](int r) {
-                const double sr = spk[r];
-                if (sr == 0.0) return 0.0;
-                double del;
-                if (K == KIND_TSVD) {
-                    const double dr = key[r];
-                    if (pi >= 0) {
-                        const double di = S.pd[pi];
-                        del = (dr - di) * (dr + di);
-                    } else {
-                        del = fma(dr, dr, -sig);
-                    }
-                } else {
-                    del = key[r] - sig;
-                }
-                return sr * rcp(del - mu);
-            };
-            // Pass 1 stores x in the column and sums x^2 in sorted order (so the
-            // norm does not depend on the order of the input rows); pass 2
-            // scales in place.
-            double s = 0.0;
-            for (int q = lane; q < n1; q += 32) {
-                const int r = S.perm[q];
-                const double x = comp(r);
-                col[r] = x;
-                s = fma(x, x, s);
-            }
-            s = warp_sum(s) + (last_row ? 1.0 : 0.0);
-            double inv, scale = 1.0;
-            bool stored = true;
-            if (isfinite(s) && s > 0x1p-960) {
-                inv = 1.0 / sqrt(s);
-            } else {
-                // rescale by the largest component to avoid overflow/underflow
-                stored = false;
-                double xm = last_row ? 1.0 : 0.0;
-                for (int r = lane; r < n1; r += 32) xm = fmax(xm, fabs(comp(r)));
-                xm = warp_max(xm);
-                scale = 1.0 / xm;
-                double s2 = 0.0;
-                for (int q = lane; q < n1; q += 32) {
-                    const double x = comp(S.perm[q]) * scale;
-                    s2 = fma(x, x, s2);
-                }
-                s2 = warp_sum(s2) + (last_row ? scale * scale : 0.0);
-                inv = 1.0 / sqrt(s2);
-            }
-            // DPR1 with rho < 0 solved -M: q ~ (D - lambda)^{-1} u needs a sign flip
-            const double vs = (K == KIND_DPR1 && sgn < 0.0) ? -1.0 : 1.0;
-            __syncwarp();
-            for (int r = lane; r < n1; r += 32) {
-                const double x = stored ? col[r] : comp(r) * scale;
-                const double v = vs * x * inv;
-                col[r] = v;
-                if (ucol) ucol[r] = sv * v / key[r];      // u_j = s v_j / d_j
-            }
-            if (last_row && lane == 0) {
-                const double vn = -scale * inv;
-                col[n1] = vn;
-                if (ucol) ucol[n1] = alpha * vn / sv;    // u_n = alpha v_n / s
-            }
-        } else {
-            const int u = item - ncomp;
-            const int row = S.drow[u];
-            const double kv = key[row];
-            const double value = K == KIND_TSVD ? kv : (K == KIND_DPR1 ? sgn * kv : kv);
-            if (lane == 0) {
-                out.lambda[pos] = value;
-                if (out.shift) out.shift[pos] = value;
-                if (out.mu) out.mu[pos] = 0.0;
-                if (out.dg_b) out.dg_b[pos] = NAN;
-                if (out.dg_Kb) out.dg_Kb[pos] = 0.0;
-                if (out.dg_Knu) out.dg_Knu[pos] = 1.0;
-                if (out.dg_iters) out.dg_iters[pos] = 0;
-                if (out.dg_flags) out.dg_flags[pos] = AE_FLAG_DEFLATED;
-            }
-            if (!col) continue;
-            for (int r = lane; r < n; r += 32) col[r] = 0.0;
-            __syncwarp();
-            if (S.kind[row] == 1) {
-                if (lane == 0) col[row] = 1.0;
-            } else {
-                run_column(S, spk, row, lane, col, 1.0);
-            }
-            if (ucol) {
-                // B v = d_r v for a deflated right vector (its last entry is 0)
-                __syncwarp();
-                for (int r = lane; r < n; r += 32) ucol[r] = col[r];
-            }
-        }
-    }
+    const int nitems = S.cnt[C_M] + 1 + S.cnt[C_ND];
+    for (int item = warp; item < nitems; item += nwarps)
+        vector_item<K>(n, n1, key, spk, z, alpha, sgn, S, out, item, lane);
 }
 
 __global__ void k_debug_rcp(int n, const double *x, double *y) {

@@ -1,0 +1,136 @@
+"""Batched arrowheads (one persistent launch per stage, CUDA-graph plans, tuner).
+
+Every instance of a batch of uneven orders is checked against the CPU oracle at
+10 n eps64; instances solved inside the batch equal those solved alone by
+arrow_eig (bitwise where both use 32-lane teams, else within tolerance); a
+captured plan replays correctly after its inputs change in place; per-instance
+status isolates a bad instance; the tuner writes its JSON cache.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from parity import assert_parity
+from paper_1302_7203_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ae():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1302_7203_gb300 import arrowhead, build
+    build.build()
+    return arrowhead
+
+
+def small_batch(count=60, lo=2, hi=700, seed=12):
+    sizes = W.batch_sizes(count, lo=max(lo, 2), hi=hi, seed=seed)
+    return [W.uniform_arrow(int(n), seed=seed * 1000 + i) for i, n in enumerate(sizes)]
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_parity_against_oracle(ae, graph):
+    inst = small_batch()
+    # a few special instances: order 1, a graded one, deflation
+    inst.append((np.zeros(0), np.zeros(0), 1.5))
+    inst.append(W.graded_arrow(300, seed=77))
+    inst.append((np.array([3.0, 1.0, 3.0, -2.0]), np.array([1.0, 0.0, -0.5, 2.0]), 0.25))
+    B = ae.Batch(inst, graph=graph)
+    info = B.run(info=True)
+    torch.cuda.synchronize()
+    assert info["n_capped"] == 0
+    st = B.status.cpu().numpy()
+    assert np.all(st == 0)
+    for i, (d, z, a) in enumerate(inst):
+        n = len(d) + 1
+        o = oracle.arrow_eig(d, z, a)
+        assert_parity(B.lam(i).cpu().numpy(), B.V(i).cpu().numpy(), o, n,
+                      what=f"batch instance {i} (n={n})")
+    B.close()
+
+
+def test_batch_equals_single_solves(ae):
+    inst = small_batch(count=24, lo=8, hi=2000, seed=5)
+    B = ae.Batch(inst)
+    B.run()
+    torch.cuda.synchronize()
+    for i, (d, z, a) in enumerate(inst):
+        n = len(d) + 1
+        r = ae.arrow_eig(torch.as_tensor(d, device="cuda"), torch.as_tensor(z, device="cuda"), a)
+        lam1, V1 = r["lam"].cpu().numpy(), r["V"].cpu().numpy()
+        lamb, Vb = B.lam(i).cpu().numpy(), B.V(i).cpu().numpy()
+        if ae.lib().ae_team_width(n) == 32:
+            np.testing.assert_array_equal(lamb, lam1)
+            np.testing.assert_array_equal(Vb, V1)
+        else:
+            tol = 10 * n * 2.0 ** -53
+            assert np.all(np.abs(lamb - lam1) <= tol * np.abs(lam1))
+            assert np.all(np.abs(Vb - V1) <= tol * np.abs(V1) + 1e-300)
+    B.close()
+
+
+def test_graph_replay_after_inputs_change(ae):
+    inst = small_batch(count=16, lo=4, hi=300, seed=9)
+    B = ae.Batch(inst)
+    B.run()
+    lam_a = B.lam_all.clone()
+    B.run()
+    torch.cuda.synchronize()
+    assert torch.equal(lam_a, B.lam_all)          # replay is deterministic
+    # new contents in the same buffers: scale every instance by 4
+    B.d_all.mul_(4.0)
+    B.z_all.mul_(4.0)
+    B.alpha_all.mul_(4.0)
+    B.run()
+    torch.cuda.synchronize()
+    assert torch.equal(B.lam_all, lam_a * 4.0)
+    B.close()
+
+
+def test_status_isolates_bad_instance(ae):
+    inst = small_batch(count=8, lo=4, hi=100, seed=3)
+    d, z, a = inst[3]
+    d = d.copy()
+    d[1] = np.nan
+    inst[3] = (d, z, a)
+    B = ae.Batch(inst)
+    B.run()
+    torch.cuda.synchronize()
+    st = B.status.cpu().numpy()
+    assert st[3] == ae.AE_ERR_INPUT
+    assert np.all(np.delete(st, 3) == 0)
+    for i in (0, 7):
+        dd, zz, aa = inst[i]
+        o = oracle.arrow_eig(dd, zz, aa)
+        assert_parity(B.lam(i).cpu().numpy(), B.V(i).cpu().numpy(), o, len(dd) + 1,
+                      what=f"instance {i} next to a bad one")
+    B.close()
+
+
+def test_autotune_writes_cache(ae, tmp_path, monkeypatch):
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("AE_TUNE_CACHE", str(path))
+    # the library reads the cache once per process; the tuner updates it in place
+    choice = ae.autotune(n_max=1024)
+    assert path.exists()
+    data = json.loads(path.read_text())
+    assert "key" in data and set(data["team"]) >= {"32", "64", "128", "256", "512", "1024"}
+    assert all(v in (8, 16, 32) for v in data["team"].values())
+    assert choice[512] == 32
+    # a batch built now uses the tuned widths and still matches the oracle
+    inst = small_batch(count=20, lo=16, hi=300, seed=31)
+    B = ae.Batch(inst)
+    B.run()
+    torch.cuda.synchronize()
+    for i in (0, 5, 19):
+        d, z, a = inst[i]
+        assert_parity(B.lam(i).cpu().numpy(), B.V(i).cpu().numpy(), oracle.arrow_eig(d, z, a),
+                      len(d) + 1, what=f"tuned instance {i}")
+    B.close()
