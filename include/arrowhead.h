@@ -248,6 +248,61 @@ int ae_autotune(int n_max, void *stream);
 int ae_team_width(int n);
 
 /*
+ * Serving: a request loop with continuous batching.  A worker thread keeps
+ * `max_inflight` CUDA streams; each tick it retires finished requests and
+ * admits queued ones (FIFO) while a stream is free and the device-memory budget
+ * covers the request's scratch and results.  Admitted requests of any kind and
+ * size run concurrently on their streams; results stay on the device, owned by
+ * the server, until released.  Latency is submit -> observed completion.
+ * The solves are those of arrow_eig / dpr1_eig / tri_arrow_svd.
+ */
+#define AE_KIND_ARROW 0
+#define AE_KIND_DPR1 1
+#define AE_KIND_SVD 2
+#define AE_EAGAIN 1005        /* queue full (submit), or result not ready */
+#define AE_REQ_QUEUED 0
+#define AE_REQ_RUNNING 1
+#define AE_REQ_DONE 2
+#define AE_REQ_ERROR 3
+
+typedef struct ae_request {
+    int kind;            /* AE_KIND_* */
+    int n;               /* matrix order */
+    const double *d;     /* device: poles (n-1; DPR1: n), caller-owned until DONE/ERROR */
+    const double *z;     /* device: spikes (n-1), DPR1: u (n) */
+    double alpha;        /* corner (arrow, SVD) or rho (DPR1) */
+    int want_vectors;    /* 1: V (and U for SVD) as well */
+} ae_request;
+
+typedef struct ae_serve_stats_t {
+    long long submitted, admitted, completed, rejected, failed, queued, running;
+    size_t bytes_in_use;
+    long long eigenpairs;       /* completed eigen/singular pairs */
+    double p50_s, p99_s, max_s; /* latency percentiles of completed requests */
+    double eigenpairs_per_s;    /* completed pairs / (last completion - first submit) */
+    int cuda_error;             /* a CUDA error the worker met, else 0 */
+} ae_serve_stats_t;
+
+typedef struct ae_server ae_server;
+/* budget: bytes of device memory for scratch + held results; queue_cap: bound
+   on waiting requests (submit returns AE_EAGAIN beyond it). */
+int ae_serve_create(ae_server **srv, size_t hbm_budget_bytes, int max_inflight, int queue_cap,
+                    const ae_opts *opts);
+int ae_serve_submit(ae_server *srv, const ae_request *req, unsigned long long *ticket);
+/* state: AE_REQ_*; latency_s of a finished request, else -1.  Returns the
+   request's error status when state is AE_REQ_ERROR. */
+int ae_serve_poll(ae_server *srv, unsigned long long ticket, int *state, double *latency_s);
+/* Device pointers to a DONE request's results (lambda / sigma, V or Q, U);
+   valid until ae_serve_release. */
+int ae_serve_result(ae_server *srv, unsigned long long ticket, const double **lambda,
+                    const double **V, const double **U);
+/* Free a finished request and its results (AE_EAGAIN while it runs). */
+int ae_serve_release(ae_server *srv, unsigned long long ticket);
+int ae_serve_stats(ae_server *srv, ae_serve_stats_t *stats);
+/* Stop the worker, wait for running requests, free everything. */
+int ae_serve_destroy(ae_server *srv);
+
+/*
  * arrow_eig_host -- arrow_eig on HOST buffers: copies d and z to the device,
  * solves, and copies lambda (and V, shift, mu when non-NULL) back, all on
  * `stream`, then synchronises.  Host buffers should be pinned for full

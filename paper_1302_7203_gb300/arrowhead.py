@@ -31,7 +31,12 @@ FLAG_CAPPED, FLAG_SINGULAR, FLAG_FP32_FALLBACK = 16, 32, 64
 EXPORTED = ["ae_default_opts", "ae_status_string", "ae_last_cuda_error", "arrow_eig",
             "dpr1_eig", "tri_arrow_svd", "arrow_eig_batched", "ae_batch_create",
             "ae_batch_run", "ae_batch_info", "ae_batch_destroy", "ae_autotune",
-            "ae_team_width", "arrow_eig_host", "arrow_eig_noalloc", "ae_debug_rcp"]
+            "ae_team_width", "ae_serve_create", "ae_serve_submit", "ae_serve_poll",
+            "ae_serve_result", "ae_serve_release", "ae_serve_stats", "ae_serve_destroy",
+            "arrow_eig_host", "arrow_eig_noalloc", "ae_debug_rcp"]
+AE_EAGAIN = 1005
+KIND_ARROW, KIND_DPR1, KIND_SVD = 0, 1, 2
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
 AE_ERR_TOO_LARGE = 1004
 
 
@@ -51,6 +56,22 @@ class AeInfo(ctypes.Structure):
                 ("max_Knu", ctypes.c_double), ("ms_reduce", ctypes.c_float),
                 ("ms_eig", ctypes.c_float), ("ms_fix", ctypes.c_float),
                 ("ms_vectors", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AeRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("d", ctypes.c_void_p),
+                ("z", ctypes.c_void_p), ("alpha", ctypes.c_double), ("want_vectors", ctypes.c_int)]
+
+
+class AeServeStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in ("submitted", "admitted", "completed", "rejected",
+                                                  "failed", "queued", "running")] + \
+        [("bytes_in_use", ctypes.c_size_t), ("eigenpairs", ctypes.c_longlong),
+         ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("max_s", ctypes.c_double),
+         ("eigenpairs_per_s", ctypes.c_double), ("cuda_error", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -112,6 +133,24 @@ def lib():
         L.ae_autotune.restype = I
         L.ae_team_width.argtypes = [I]
         L.ae_team_width.restype = I
+        L.ae_serve_create.argtypes = [ctypes.POINTER(P), ctypes.c_size_t, I, I,
+                                      ctypes.POINTER(AeOpts)]
+        L.ae_serve_create.restype = I
+        L.ae_serve_submit.argtypes = [P, ctypes.POINTER(AeRequest),
+                                      ctypes.POINTER(ctypes.c_ulonglong)]
+        L.ae_serve_submit.restype = I
+        L.ae_serve_poll.argtypes = [P, ctypes.c_ulonglong, ctypes.POINTER(I),
+                                    ctypes.POINTER(D)]
+        L.ae_serve_poll.restype = I
+        L.ae_serve_result.argtypes = [P, ctypes.c_ulonglong, ctypes.POINTER(P),
+                                      ctypes.POINTER(P), ctypes.POINTER(P)]
+        L.ae_serve_result.restype = I
+        L.ae_serve_release.argtypes = [P, ctypes.c_ulonglong]
+        L.ae_serve_release.restype = I
+        L.ae_serve_stats.argtypes = [P, ctypes.POINTER(AeServeStats)]
+        L.ae_serve_stats.restype = I
+        L.ae_serve_destroy.argtypes = [P]
+        L.ae_serve_destroy.restype = I
         L.arrow_eig_noalloc.argtypes = L.arrow_eig.argtypes
         L.arrow_eig_noalloc.restype = I
         L.ae_debug_rcp.argtypes = [I, P, P, P]
@@ -371,6 +410,101 @@ class Batch:
             pass
 
 
+class _DeviceView:
+    """Zero-copy view of a device buffer for torch.as_tensor (CUDA array interface)."""
+
+    def __init__(self, ptr, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+class Server:
+    """Continuous-batching request loop over the solvers (ae_serve_*).
+
+    ``submit(kind, d, z, alpha)`` takes float64 CUDA tensors (kept referenced
+    until ``release``) and returns a ticket; ``poll`` gives (state, latency s);
+    ``result`` copies a finished request's outputs into new tensors."""
+
+    def __init__(self, budget_bytes, max_inflight=8, queue_cap=4096, opts=None):
+        self.h = ctypes.c_void_p()
+        o = opts if opts is not None else default_opts()
+        _check("ae_serve_create", lib().ae_serve_create(ctypes.byref(self.h), int(budget_bytes),
+                                                        int(max_inflight), int(queue_cap),
+                                                        ctypes.byref(o)))
+        self.refs = {}
+        self.meta = {}
+
+    def submit(self, kind, d, z, alpha, vectors=True):
+        n = int(d.numel()) + (0 if kind == KIND_DPR1 else 1)
+        req = AeRequest(kind, n, d.data_ptr() if d.numel() else None,
+                        z.data_ptr() if z.numel() else None, float(alpha), 1 if vectors else 0)
+        t = ctypes.c_ulonglong()
+        st = lib().ae_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if st == AE_EAGAIN:
+            return None
+        _check("ae_serve_submit", st)
+        self.refs[t.value] = (d, z)
+        self.meta[t.value] = (kind, n, vectors)
+        return t.value
+
+    def poll(self, ticket):
+        state = ctypes.c_int()
+        lat = ctypes.c_double()
+        lib().ae_serve_poll(self.h, ctypes.c_ulonglong(ticket), ctypes.byref(state),
+                            ctypes.byref(lat))
+        return state.value, lat.value
+
+    def wait(self, ticket, timeout=120.0):
+        import time
+        t0 = time.time()
+        while True:
+            st, lat = self.poll(ticket)
+            if st in (REQ_DONE, REQ_ERROR):
+                return st, lat
+            if time.time() - t0 > timeout:
+                raise TimeoutError(f"request {ticket} not finished")
+            time.sleep(0.0005)
+
+    def result(self, ticket):
+        import torch
+        kind, n, vectors = self.meta[ticket]
+        pl, pv, pu = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check("ae_serve_result", lib().ae_serve_result(self.h, ctypes.c_ulonglong(ticket),
+                                                        ctypes.byref(pl), ctypes.byref(pv),
+                                                        ctypes.byref(pu)))
+        out = {"lam": torch.as_tensor(_DeviceView(pl.value, (n,)), device="cuda").clone()}
+        if vectors:
+            out["V"] = torch.as_tensor(_DeviceView(pv.value, (n, n)), device="cuda").t().clone()
+            if kind == KIND_SVD:
+                out["U"] = torch.as_tensor(_DeviceView(pu.value, (n, n)),
+                                           device="cuda").t().clone()
+        return out
+
+    def release(self, ticket):
+        st = lib().ae_serve_release(self.h, ctypes.c_ulonglong(ticket))
+        if st == AE_OK:
+            self.refs.pop(ticket, None)
+            self.meta.pop(ticket, None)
+        return st
+
+    def stats(self):
+        s = AeServeStats()
+        _check("ae_serve_stats", lib().ae_serve_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self.h:
+            lib().ae_serve_destroy(self.h)
+            self.h = None
+            self.refs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def autotune(n_max=4096, stream=None):
     """Run the team-width tuner and store its choices in the JSON cache."""
     _check("ae_autotune", lib().ae_autotune(int(n_max), _stream_handle(stream)))
@@ -425,7 +559,8 @@ def exported_symbols(path=LIB_PATH):
     return [s for s in EXPORTED if hasattr(L, s)]
 
 
-__all__ = ["arrow_eig", "dpr1_eig", "tri_arrow_svd", "Batch", "autotune", "arrow_eig_host",
+__all__ = ["arrow_eig", "dpr1_eig", "tri_arrow_svd", "Batch", "Server", "autotune",
+           "arrow_eig_host",
            "debug_rcp", "default_opts", "lib", "AeOpts",
            "AeInfo", "AeDiag", "AeError", "exported_symbols", "EXPORTED"]
 

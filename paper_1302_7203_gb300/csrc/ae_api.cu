@@ -94,6 +94,7 @@ const char *ae_status_string(int status) {
         case AE_ERR_CUDA: return "CUDA error";
         case AE_ERR_INPUT: return "non-finite input";
         case AE_ERR_NOCONV: return "iteration cap reached";
+        case AE_EAGAIN: return "queue full or result not ready (try again)";
         case AE_ERR_TOO_LARGE:
             return "n too large for the static scratch of arrow_eig_noalloc "
                    "(AE_NOALLOC_SCRATCH_BYTES)";
