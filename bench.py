@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the DPR1 / SVD / batched / serving measurements")
+    p.add_argument("--serve-requests", type=int, default=120)
     return p.parse_args()
 
 
@@ -142,6 +145,126 @@ def max_err_neps(lam, Vcols, res, n):
     ev = np.max(np.abs(Vcols - res["V"]) /
                 np.maximum(np.abs(res["V"]), np.finfo(float).tiny)) / (n * eps)
     return {"lambda": float(el), "vectors": float(ev), "bound": 10.0}
+
+
+def timed_device(fn, steps, warmup, stream, flush):
+    """Device time (ms per step) of fn() over `steps` runs after `warmup`."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for i in range(steps):
+        flush.fill_(i & 0xff)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / steps
+
+
+def extras(arrowhead, W, dev, stream, flush, args):
+    """DPR1 and SVD (n = 8192), the batched set and a serving sweep."""
+    import torch
+    out = {}
+    prec = arrowhead.AE_FP32_BRACKET if args.precision == "fp32" else arrowhead.AE_FP64
+    opts = arrowhead.default_opts(precision=prec, profile=1)
+    n = 8192
+    d, u, rho = W.uniform_dpr1(n, seed=3)
+    dt, ut = torch.as_tensor(d, device=dev), torch.as_tensor(u, device=dev)
+    Q = torch.empty((n, n), dtype=torch.float64, device=dev)
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    info = {}
+
+    def f_dpr1():
+        info.update(arrowhead.dpr1_eig(dt, ut, rho, opts=opts, info=True,
+                                       out={"lam": lam, "Q": Q}, stream=stream)["info"])
+    ms = timed_device(f_dpr1, 3, 1, stream, flush)
+    fl = eig_kernel_flops(n + 1, info["n_reduced"], info["total_iter"], info["fix_iter"])
+    out["dpr1_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                         "k_eig_ms": info["ms_eig"],
+                         "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+    d, z, al = W.uniform_tsvd(n, seed=4)
+    dt, zt = torch.as_tensor(d, device=dev), torch.as_tensor(z, device=dev)
+    U = torch.empty((n, n), dtype=torch.float64, device=dev)
+
+    def f_svd():
+        info.update(arrowhead.tri_arrow_svd(dt, zt, al, opts=opts, info=True,
+                                            out={"s": lam, "U": U, "V": Q}, stream=stream)["info"])
+    ms = timed_device(f_svd, 3, 1, stream, flush)
+    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"])
+    out["svd_n8192"] = {"value": n / (ms / 1e3), "unit": "singular triplets/s", "ms_per_step": ms,
+                        "k_eig_ms": info["ms_eig"],
+                        "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+    del Q, U
+    # batched: 4096 instances, orders log-uniform in [32, 4096], one CUDA-graph plan
+    inst = W.uniform_batch(4096, seed=2)
+    B = arrowhead.Batch(inst, opts=arrowhead.default_opts(precision=prec), stream=stream)
+    ms = timed_device(lambda: B.run(), 2, 1, stream, flush)
+    binfo = B.run(info=True)
+    tot_n = int(B.n_off[-1])
+    out["batched_4096"] = {"value": tot_n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                           "instances": len(inst), "eigenpairs": tot_n,
+                           "sum_n2": int((B.n.astype(np.int64) ** 2).sum()),
+                           "fp64_steps_per_eigenpair": binfo["total_iter"] / tot_n,
+                           "team_widths": {str(b): arrowhead.lib().ae_team_width(b)
+                                           for b in (32, 64, 128, 256, 512)}}
+    B.close()
+    del B
+    torch.cuda.empty_cache()
+    # serving: Poisson arrivals of mixed kinds, orders log-uniform in [64, 16384]
+    out["serving"] = serve_sweep(arrowhead, W, dev, args.serve_requests, prec)
+    return out
+
+
+def serve_sweep(arrowhead, W, dev, count, prec):
+    import torch
+    res = {}
+    for rate in (20.0, 200.0, 2000.0):
+        t_arr, kinds, ns = W.serve_stream(rate, count, seed=5)
+        reqs = []
+        for i, (k, n) in enumerate(zip(kinds, ns)):
+            if k == 0:
+                d, z, a = W.uniform_arrow(int(n), seed=10_000 + i)
+            elif k == 1:
+                d, z, a = W.uniform_dpr1(int(n), seed=10_000 + i)
+            else:
+                d, z, a = W.uniform_tsvd(int(n), seed=10_000 + i)
+            reqs.append((int(k), torch.as_tensor(d, device=dev), torch.as_tensor(z, device=dev), a))
+        srv = arrowhead.Server(budget_bytes=96 << 30, max_inflight=16, queue_cap=1 << 16,
+                               opts=arrowhead.default_opts(precision=prec))
+        t0 = time.perf_counter()
+        pending = []
+        i = 0
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and t_arr[i] <= now:
+                k, dt, zt, a = reqs[i]
+                tk = srv.submit(k, dt, zt, a, vectors=True)
+                if tk is not None:
+                    pending.append(tk)
+                i += 1
+            still = []
+            for tk in pending:
+                st, _ = srv.poll(tk)
+                if st in (arrowhead.REQ_DONE, arrowhead.REQ_ERROR):
+                    srv.release(tk)
+                else:
+                    still.append(tk)
+            pending = still
+            time.sleep(0.0002)
+        st = srv.stats()
+        srv.close()
+        res[f"{int(rate)}/s"] = {"p50_ms": 1e3 * st["p50_s"], "p99_ms": 1e3 * st["p99_s"],
+                                 "eigenpairs_per_s": st["eigenpairs_per_s"],
+                                 "completed": st["completed"], "rejected": st["rejected"],
+                                 "failed": st["failed"]}
+    res["requests_per_rate"] = count
+    res["mix"] = "arrow/DPR1/SVD uniform, orders log-uniform [64, 16384], vectors kept on device"
+    return res
 
 
 def run_reference(args, rank, world):
@@ -274,13 +397,19 @@ def main():
         e2e = {"value": world * n * ne / te, "unit": UNIT,
                "h2d_bytes_per_step": 2 * (n - 1) * 8, "d2h_bytes_per_step": (n + n * n) * 8}
 
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu, ks, ores = cpu_baseline(d, z, alpha, n, args.cpu_seconds)
+        kt = torch.as_tensor(ks, device=dev)
+        err = max_err_neps(lam[kt].cpu().numpy(), V[kt].t().cpu().numpy(), ores, n)
+    extra = None
+    if world == 1 and not args.no_extras:
+        del V
+        torch.cuda.empty_cache()
+        extra = extras(arrowhead, W, dev, stream, flush, args)
+
     if rank == 0:
-        cpu = None
-        err = None
-        if world == 1 and not args.no_cpu:
-            cpu, ks, ores = cpu_baseline(d, z, alpha, n, args.cpu_seconds)
-            kt = torch.as_tensor(ks, device=dev)
-            err = max_err_neps(lam[kt].cpu().numpy(), V[kt].t().cpu().numpy(), ores, n)
         name = {P64: "fp64", P32: "fp32_bracket"}
         variants = {}
         for prec, tot, inf in ((primary, total_ms, infos), (other, total_o, infos_o)):
@@ -298,7 +427,7 @@ def main():
                            "l2": "512 MiB write between steps (L2 flush)",
                            "parallelism": f"{world} independent instances"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
-                "max_err_neps": err, "variants": variants,
+                "max_err_neps": err, "variants": variants, "extras": extra,
                 "clocks": clk.summary(), "gpu_launches": LAUNCHES_PER_STEP * args.steps,
                 "phases_ms": {k: float(np.mean([x[k] for x in infos]))
                               for k in ("ms_reduce", "ms_eig", "ms_fix", "ms_vectors")},
