@@ -122,6 +122,16 @@ static int solve_common(ae::Kind kind, int n, const double *d, const double *z, 
     cudaError_t e = cudaMallocAsync(&base, ae::arrow_scratch_bytes(n), st);
     if (e != cudaSuccess) return cuda_fail(e);
     ae::Scratch S = ae::carve_scratch(base, n);
+    // one slice of n stored (delta_j, c_j) pairs per warp of the eigenvalue kernel
+    void *wb = nullptr;
+    const long long wstride = ((long long)n + 1) & ~1LL;
+    e = cudaMallocAsync(&wb, sizeof(double2) * wstride * ae::eig_grid_warps(n), st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(base, st);
+        return cuda_fail(e);
+    }
+    S.wbuf = (double2 *)wb;
+    S.wstride = wstride;
     int status = AE_OK;
     e = ae::launch_solve(kind, n, d, z, alpha, rho, out, ro, S, st);
     if (e != cudaSuccess) status = cuda_fail(e);
@@ -158,6 +168,8 @@ static int solve_common(ae::Kind kind, int n, const double *d, const double *z, 
             else if (cnt[ae::C_CAPPED]) status = AE_ERR_NOCONV;
         }
     }
+    e = cudaFreeAsync(wb, st);
+    if (e != cudaSuccess && status == AE_OK) status = cuda_fail(e);
     e = cudaFreeAsync(base, st);
     if (e != cudaSuccess && status == AE_OK) status = cuda_fail(e);
     return status;

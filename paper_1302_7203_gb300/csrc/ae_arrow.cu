@@ -115,12 +115,14 @@ __global__ void __launch_bounds__(256) k_eig(Scratch S, SolveOpts o) {
     const int ncomp = m + 1;
     const auto R = PolesOf<K>::make(S, m);
     const WarpTeam T{lane};
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    double2 *buf = S.wbuf ? S.wbuf + gw * S.wstride : nullptr;
     for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(S.cnt + C_WORK, 1);
         k = __shfl_sync(FULL, k, 0);
         if (k >= ncomp) break;
-        eig_item<K>(R, T, S, k, o);
+        eig_item<K>(R, T, S, k, o, buf);
     }
 }
 
@@ -223,6 +225,8 @@ static size_t layout(uintptr_t base, int n, Scratch *S) {
     T.es_fixpole = (int *)take(sizeof(int) * nn);
     T.fixlist = (int *)take(sizeof(int) * nn);
     T.pos = (int *)take(sizeof(int) * nn);
+    T.wbuf = nullptr;
+    T.wstride = 0;
     if (S) *S = T;
     return (size_t)(p - start);
 }
@@ -250,12 +254,25 @@ static int sm_count() {
     return cached;
 }
 
+// CTAs of k_eig: enough for every eigenpair, at most what stays resident
+static int eig_grid(int n) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eig<KIND_ARROW>, 256, 0);
+        if (per_sm <= 0) per_sm = 1;
+    }
+    const int want = (n + 7) / 8;
+    const int cap = sm_count() * per_sm;
+    return want < cap ? want : cap;
+}
+
+int eig_grid_warps(int n) { return eig_grid(n) * 8; }
+
 template <Kind K>
 static void launch_eig_kernels(int n, Scratch S, const SolveOpts &so, const RunOpts &ro,
                                cudaStream_t st) {
     const int sms = sm_count();
-    int grid = (n + 7) / 8;
-    grid = grid < sms * 8 ? grid : sms * 8;
+    const int grid = eig_grid(n);
     if (ro.ev[1]) cudaEventRecord(ro.ev[1], st);
     k_eig<K><<<grid, 256, 0, st>>>(S, so);
     if (ro.ev[2]) cudaEventRecord(ro.ev[2], st);

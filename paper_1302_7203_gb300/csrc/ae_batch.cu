@@ -147,26 +147,32 @@ __global__ void __launch_bounds__(1024) k_batch_prep(const BatchInst *__restrict
     post_block<KIND_ARROW>(n1, B.d, B.z, *B.alpha, 0.0, S);
 }
 
+// buf: this warp's 4 slices of stored (delta_j, c_j) pairs, `stride` apart
 template <int W>
 __device__ __forceinline__ void batch_unit(const BatchInst &B, long long unit_in_inst, int lane,
-                                           const SolveOpts &o) {
+                                           const SolveOpts &o, double2 *buf, long long stride) {
     constexpr int EPW = 32 / W;
     const int m = B.S.cnt[C_M];
-    const int k = (int)(unit_in_inst * EPW) + lane / W;
+    const int g = lane / W;
+    const int k = (int)(unit_in_inst * EPW) + g;
     const auto R = PolesOf<KIND_ARROW>::make(B.S, m);
+    double2 *tb = buf ? buf + g * stride : nullptr;
     if (W == 32) {
-        if (k <= m) eig_item<KIND_ARROW>(R, WarpTeam{lane}, B.S, k, o);
+        if (k <= m) eig_item<KIND_ARROW>(R, WarpTeam{lane}, B.S, k, o, tb);
     } else {
         const unsigned mask = ((1u << W) - 1u) << (lane & ~(W - 1));
-        if (k <= m) eig_item<KIND_ARROW>(R, SubWarpTeam<W>{lane & (W - 1), mask}, B.S, k, o);
+        if (k <= m) eig_item<KIND_ARROW>(R, SubWarpTeam<W>{lane & (W - 1), mask}, B.S, k, o, tb);
     }
 }
 
 __global__ void __launch_bounds__(256) k_batch_eig(const BatchInst *__restrict__ I, int count,
                                                    const long long *__restrict__ uoff,
-                                                   BatchCtl *ctl, SolveOpts o) {
+                                                   BatchCtl *ctl, SolveOpts o, double2 *wbuf,
+                                                   long long wstride) {
     const int lane = threadIdx.x & 31;
     const long long total = uoff[count];
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    double2 *buf = wbuf ? wbuf + gw * 4 * wstride : nullptr;
     for (;;) {
         long long u = 0;
         if (lane == 0) u = atomicAdd(&ctl->tick_eig, 1);
@@ -176,9 +182,9 @@ __global__ void __launch_bounds__(256) k_batch_eig(const BatchInst *__restrict__
         const BatchInst &B = I[i];
         const long long ui = u - uoff[i];
         switch (B.team) {
-            case 8: batch_unit<8>(B, ui, lane, o); break;
-            case 16: batch_unit<16>(B, ui, lane, o); break;
-            default: batch_unit<32>(B, ui, lane, o); break;
+            case 8: batch_unit<8>(B, ui, lane, o, buf, wstride); break;
+            case 16: batch_unit<16>(B, ui, lane, o, buf, wstride); break;
+            default: batch_unit<32>(B, ui, lane, o, buf, wstride); break;
         }
         __syncwarp();
     }
@@ -345,9 +351,20 @@ static int sm_count_b() {
     return c > 0 ? c : 1;
 }
 
+static int batch_eig_grid() {
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_eig, 256, 0);
+        if (per_sm <= 0) per_sm = 1;
+    }
+    return sm_count_b() * per_sm;
+}
+
 struct Plan {
     int count = 0;
     long long total_n = 0;
+    double2 *wbuf = nullptr;     // 4 slices of stored pairs per warp of k_batch_eig
+    long long wstride = 0;
     BatchInst *d_inst = nullptr;
     long long *d_eoff = nullptr, *d_uoff = nullptr;
     int2 *d_fix = nullptr;
@@ -363,7 +380,8 @@ struct Plan {
 static void enqueue(const Plan &P, cudaStream_t st) {
     const int sms = sm_count_b();
     k_batch_prep<<<P.count, 1024, 0, st>>>(P.d_inst, P.d_ctl);
-    k_batch_eig<<<sms * 8, 256, 0, st>>>(P.d_inst, P.count, P.d_uoff, P.d_ctl, P.so);
+    k_batch_eig<<<batch_eig_grid(), 256, 0, st>>>(P.d_inst, P.count, P.d_uoff, P.d_ctl, P.so,
+                                                  P.wbuf, P.wstride);
     const unsigned g = (unsigned)((P.total_n + 255) / 256);
     if (P.ro.fixup) {
         k_batch_fix_decide<<<g, 256, 0, st>>>(P.d_inst, P.count, P.d_eoff, P.d_fix, P.d_ctl,
@@ -384,6 +402,7 @@ static void free_plan(Plan *P) {
     cudaFree(P->d_fix);
     cudaFree(P->d_ctl);
     cudaFree(P->scratch);
+    cudaFree(P->wbuf);
     delete P;
 }
 
@@ -410,6 +429,12 @@ static cudaError_t build_plan(Plan *P, int count, const long long *n_off, const 
     if ((e = cudaMalloc(&P->d_fix, sizeof(int2) * (size_t)(P->total_n > 0 ? P->total_n : 1))))
         return e;
     if ((e = cudaMalloc(&P->d_ctl, sizeof(BatchCtl)))) return e;
+    long long nmax = 1;
+    for (int i = 0; i < count; ++i) nmax = std::max(nmax, n_off[i + 1] - n_off[i]);
+    P->wstride = (nmax + 1) & ~1LL;
+    if ((e = cudaMalloc(&P->wbuf, sizeof(double2) * P->wstride * 4 *
+                                      (size_t)batch_eig_grid() * 8)))
+        return e;
     P->host.resize(count);
     std::vector<long long> uoff(count + 1, 0);
     long long vo = 0;

@@ -62,6 +62,8 @@ struct Scratch {
     double *es_sigma, *es_mu, *es_lam, *es_b, *es_Kb, *es_Knu, *es_fixshift;
     int *es_pole, *es_iters, *es_flags, *es_fixpole, *fixlist;
     int *pos;       // output position of computed (first m+1) and deflated items
+    double2 *wbuf;  // optional: one (delta_j, c_j) slice per eig team, wstride apart
+    long long wstride;
 };
 
 struct Outputs {
@@ -84,6 +86,9 @@ struct RunOpts {
 };
 
 size_t arrow_scratch_bytes(int n);
+// warps of the eigenvalue kernel for order n (the stored-pair buffer holds one
+// slice of n pairs per warp)
+int eig_grid_warps(int n);
 Scratch carve_scratch(void *base, int n);
 // Issue a whole solve on `st`.  ARROW: d, z have n-1 entries; DPR1: d, u (in z)
 // have n entries and rho is used; SVD: d, z have n-1 entries.

@@ -275,7 +275,8 @@ __device__ __forceinline__ void record_stats(const Scratch &S, const EigResult &
 // stores the result.
 template <Kind K, class Team>
 __device__ __forceinline__ void eig_item(const typename PolesOf<K>::type &R, const Team &T,
-                                         const Scratch &S, int k, const SolveOpts &o) {
+                                         const Scratch &S, int k, const SolveOpts &o,
+                                         double2 *buf = nullptr) {
     const int m = R.m;
     EigResult res;
     if (m == 0) {
@@ -284,7 +285,7 @@ __device__ __forceinline__ void eig_item(const typename PolesOf<K>::type &R, con
     } else {
         int i, side;
         select_shift(R, T, k, i, side);
-        res = solve_shifted(R, T, i, side, o);
+        res = solve_shifted(R, T, i, side, o, buf);
     }
     if (T.rank == 0) {
         store_result(S, k, res);

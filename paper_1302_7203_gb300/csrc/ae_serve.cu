@@ -39,6 +39,7 @@ struct Req {
     size_t bytes = 0;           // scratch + results charged to the budget
     bool charged = false;       // bytes are counted in in_use
     void *scratch = nullptr;
+    void *wbuf = nullptr;       // stored (delta_j, c_j) pairs of the eigenvalue kernel
     double *result = nullptr;   // lambda | V | U in one block
     double *lam = nullptr, *V = nullptr, *U = nullptr;
     int slot = -1;
@@ -46,6 +47,10 @@ struct Req {
     int *cnt_host = nullptr;    // pinned copy of the solve's counters
     clk::time_point t_submit, t_done;
 };
+
+size_t wbuf_bytes(int n) {
+    return sizeof(double2) * (size_t)((n + 1) & ~1) * (size_t)ae::eig_grid_warps(n);
+}
 
 size_t result_doubles(const ae_request &r) {
     const size_t n = (size_t)r.n;
@@ -94,11 +99,15 @@ bool ae_server::admit_locked(Req *r) {
     const ae_request &q = r->in;
     const ae::Kind kind = q.kind == AE_KIND_DPR1 ? ae::KIND_DPR1
                         : q.kind == AE_KIND_SVD ? ae::KIND_TSVD : ae::KIND_ARROW;
+    const long long wstride = ((long long)q.n + 1) & ~1LL;
     cudaError_t e = cudaMallocAsync(&r->scratch, ae::arrow_scratch_bytes(q.n), st);
+    if (!e) e = cudaMallocAsync(&r->wbuf, wbuf_bytes(q.n), st);
     if (!e) e = cudaMallocAsync((void **)&r->result, sizeof(double) * result_doubles(q), st);
     if (e) {                       // out of device memory now: retry later
         if (r->scratch) cudaFreeAsync(r->scratch, st);
+        if (r->wbuf) cudaFreeAsync(r->wbuf, st);
         r->scratch = nullptr;
+        r->wbuf = nullptr;
         r->result = nullptr;
         cudaGetLastError();
         return false;
@@ -108,6 +117,8 @@ bool ae_server::admit_locked(Req *r) {
     r->V = q.want_vectors ? r->result + n : nullptr;
     r->U = (q.want_vectors && q.kind == AE_KIND_SVD) ? r->result + n + n * n : nullptr;
     ae::Scratch S = ae::carve_scratch(r->scratch, q.n);
+    S.wbuf = (double2 *)r->wbuf;
+    S.wstride = wstride;
     ae::Outputs out{};
     out.lambda = r->lam;
     out.V = r->V;
@@ -119,8 +130,10 @@ bool ae_server::admit_locked(Req *r) {
     if (!e) e = cudaMemcpyAsync(r->cnt_host, S.cnt, sizeof(int) * ae::C_COUNT,
                                 cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaFreeAsync(r->scratch, st);
+    if (!e) e = cudaFreeAsync(r->wbuf, st);
     if (!e) e = cudaEventRecord(r->done, st);
     r->scratch = nullptr;
+    r->wbuf = nullptr;
     if (e) {
         r->state = AE_REQ_ERROR;
         r->status = AE_ERR_CUDA;
@@ -235,7 +248,7 @@ int ae_serve_submit(ae_server *s, const ae_request *req, unsigned long long *tic
     if (!isfinite(q.alpha) || (q.kind == AE_KIND_SVD && q.alpha == 0.0)) return -2;
     Req *r = new Req();
     r->in = q;
-    r->bytes = ae::arrow_scratch_bytes(q.n) + sizeof(double) * result_doubles(q);
+    r->bytes = ae::arrow_scratch_bytes(q.n) + wbuf_bytes(q.n) + sizeof(double) * result_doubles(q);
     if (cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost((void **)&r->cnt_host, sizeof(int) * ae::C_COUNT) != cudaSuccess) {
         if (r->done) cudaEventDestroy(r->done);
