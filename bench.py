@@ -13,9 +13,16 @@ e2e        the same metric through arrow_eig_host: pinned host d, z in, lambda
            and V (2 GiB) out, copies inside the timed region.
 roofline   the eigenvalue kernel (k_eig): algorithmic FP64 flops per launch
            (3 per term per bisection step: subtract, divide, add, as in
-           Algorithm 3; 3 per term for the shift choice; 20 per term for the
+           Algorithm 3; 6 per term per Newton step, which adds the derivative
+           term; 3 per term for the shift choice; 20 per term for the
            double-double element b) over its event-timed duration, against the
-           FP64 ALU peak 152 SMs x 4 flop/clk x 2070 MHz.
+           FP64 ALU peak 152 SMs x 4 flop/clk x 2070 MHz.  Also reported: the
+           all-FP64 bisection's algorithmic work over the headline form's k_eig
+           time (fp64_bisection_equivalent_tflops).
+forms      fp32 (default headline): FP32 opening bracket, FP64 bisection;
+           fp64: all-FP64 bisection; fp32_newton / fp64_newton: the same with
+           the bracketed Newton finish.  All four are timed; --form picks the
+           headline.
 cpu_baseline  the CPU oracle on a bounded sample of eigenpairs of the same
            matrix, on all host cores.
 --impl reference   times the CPU oracle alone (the reference arm).
@@ -42,6 +49,10 @@ LAUNCHES_PER_STEP = 8   # k_check k_rank k_reduce k_eig k_fix_decide k_fix_solve
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
 
 
+# solver forms: (ae_opts.precision, ae_opts.finish)
+FORMS = {"fp32": (1, 0), "fp64": (0, 0), "fp32_newton": (1, 1), "fp64_newton": (0, 1)}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -49,8 +60,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--precision", default="fp32", choices=["fp64", "fp32"],
-                   help="headline form: fp32 = FP32 opening bracket + FP64 finish")
+    p.add_argument("--form", default="fp32", choices=list(FORMS),
+                   help="headline form: fp32 = FP32 opening bracket + FP64 bisection; "
+                        "fp64 = all-FP64 bisection; *_newton = bracketed Newton finish")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -111,10 +123,14 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
-def eig_kernel_flops(n, ncomp, total_iter, fix_iter):
-    """Algorithmic FP64 flops of one k_eig launch (see module docstring)."""
+def eig_kernel_flops(n, ncomp, total_iter, fix_iter, per_eval=3.0):
+    """Algorithmic FP64 flops of one k_eig launch (see module docstring).
+
+    per_eval: flops per term of one FP64 evaluation of the secular function,
+    3 for a bisection step (sub, div, add), 6 for a Newton step (the same
+    plus the derivative term's mul, div, add)."""
     terms = n - 2                    # each O(n) pass runs over the other poles
-    return 3.0 * terms * (total_iter - fix_iter) + (3.0 + 20.0) * terms * ncomp
+    return per_eval * terms * (total_iter - fix_iter) + (3.0 + 20.0) * terms * ncomp
 
 
 def cpu_baseline(d, z, alpha, n, seconds):
@@ -170,8 +186,9 @@ def extras(arrowhead, W, dev, stream, flush, args):
     """DPR1 and SVD (n = 8192), the batched set and a serving sweep."""
     import torch
     out = {}
-    prec = arrowhead.AE_FP32_BRACKET if args.precision == "fp32" else arrowhead.AE_FP64
-    opts = arrowhead.default_opts(precision=prec, profile=1)
+    prec, fin = FORMS[args.form]
+    per_eval = 6.0 if fin == 1 else 3.0
+    opts = arrowhead.default_opts(precision=prec, finish=fin, profile=1)
     n = 8192
     d, u, rho = W.uniform_dpr1(n, seed=3)
     dt, ut = torch.as_tensor(d, device=dev), torch.as_tensor(u, device=dev)
@@ -183,7 +200,8 @@ def extras(arrowhead, W, dev, stream, flush, args):
         info.update(arrowhead.dpr1_eig(dt, ut, rho, opts=opts, info=True,
                                        out={"lam": lam, "Q": Q}, stream=stream)["info"])
     ms = timed_device(f_dpr1, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n + 1, info["n_reduced"], info["total_iter"], info["fix_iter"])
+    fl = eig_kernel_flops(n + 1, info["n_reduced"], info["total_iter"], info["fix_iter"],
+                          per_eval)
     out["dpr1_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                          "k_eig_ms": info["ms_eig"],
                          "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -195,14 +213,15 @@ def extras(arrowhead, W, dev, stream, flush, args):
         info.update(arrowhead.tri_arrow_svd(dt, zt, al, opts=opts, info=True,
                                             out={"s": lam, "U": U, "V": Q}, stream=stream)["info"])
     ms = timed_device(f_svd, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"])
+    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval)
     out["svd_n8192"] = {"value": n / (ms / 1e3), "unit": "singular triplets/s", "ms_per_step": ms,
                         "k_eig_ms": info["ms_eig"],
                         "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
     del Q, U
     # batched: 4096 instances, orders log-uniform in [32, 4096], one CUDA-graph plan
     inst = W.uniform_batch(4096, seed=2)
-    B = arrowhead.Batch(inst, opts=arrowhead.default_opts(precision=prec), stream=stream)
+    B = arrowhead.Batch(inst, opts=arrowhead.default_opts(precision=prec, finish=fin),
+                        stream=stream)
     ms = timed_device(lambda: B.run(), 2, 1, stream, flush)
     binfo = B.run(info=True)
     tot_n = int(B.n_off[-1])
@@ -216,11 +235,12 @@ def extras(arrowhead, W, dev, stream, flush, args):
     del B
     torch.cuda.empty_cache()
     # serving: Poisson arrivals of mixed kinds, orders log-uniform in [64, 16384]
-    out["serving"] = serve_sweep(arrowhead, W, dev, args.serve_requests, prec)
+    out["serving"] = serve_sweep(arrowhead, W, dev, args.serve_requests,
+                                 arrowhead.default_opts(precision=prec, finish=fin))
     return out
 
 
-def serve_sweep(arrowhead, W, dev, count, prec):
+def serve_sweep(arrowhead, W, dev, count, opts):
     import torch
     res = {}
     for rate in (20.0, 200.0, 2000.0):
@@ -235,7 +255,7 @@ def serve_sweep(arrowhead, W, dev, count, prec):
                 d, z, a = W.uniform_tsvd(int(n), seed=10_000 + i)
             reqs.append((int(k), torch.as_tensor(d, device=dev), torch.as_tensor(z, device=dev), a))
         srv = arrowhead.Server(budget_bytes=96 << 30, max_inflight=16, queue_cap=1 << 16,
-                               opts=arrowhead.default_opts(precision=prec))
+                               opts=opts)
         t0 = time.perf_counter()
         pending = []
         i = 0
@@ -327,8 +347,9 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def timed(prec):
-        opts = arrowhead.default_opts(precision=prec, profile=1)
+    def timed(form):
+        prec, fin = FORMS[form]
+        opts = arrowhead.default_opts(precision=prec, finish=fin, profile=1)
 
         def step():
             return arrowhead.arrow_eig(dt, zt, alpha, opts=opts, info=True,
@@ -359,20 +380,25 @@ def main():
             total = float(t.item())
         return total, infos, clk
 
-    P64, P32 = arrowhead.AE_FP64, arrowhead.AE_FP32_BRACKET
-    primary = P32 if args.precision == "fp32" else P64
-    other = P64 if primary == P32 else P32
-    # the other form first, so lam/V hold the headline form's results at the end
-    total_o, infos_o, _ = timed(other)
-    total_ms, infos, clk = timed(primary)
+    primary = args.form
+    # the other forms first, so lam/V hold the headline form's results at the end
+    runs = {f: timed(f) for f in FORMS if f != primary}
+    runs[primary] = timed(primary)
+    total_ms, infos, clk = runs[primary]
     value = world * n * args.steps / (total_ms / 1e3)
     info = infos[-1]
     eig_ms = float(np.mean([x["ms_eig"] for x in infos]))
-    flops = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"])
+    per_eval = 6.0 if FORMS[primary][1] == 1 else 3.0
+    flops = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval)
     achieved = flops / (eig_ms / 1e3) / 1e12
+    # the all-FP64 bisection's algorithmic work (its measured step count) over
+    # this form's k_eig time: the rate at which the paper's work gets done
+    i64 = runs["fp64"][1][-1]
+    eq = eig_kernel_flops(n, i64["n_reduced"], i64["total_iter"], i64["fix_iter"]) / (eig_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
             "kernel": "k_eig", "kernel_ms": eig_ms,
+            "fp64_bisection_equivalent_tflops": eq,
             "peak_note": "FP64 ALU: 152 SMs x 4 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)"}
 
     e2e = None
@@ -381,7 +407,7 @@ def main():
         zh = torch.as_tensor(z).pin_memory()
         lh = torch.empty(n, dtype=torch.float64).pin_memory()
         Vh = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        eopts = arrowhead.default_opts(precision=primary)
+        eopts = arrowhead.default_opts(precision=FORMS[primary][0], finish=FORMS[primary][1])
         arrowhead.arrow_eig_host(dh, zh, alpha, opts=eopts, out={"lam": lh, "V": Vh},
                                  stream=stream)
         t0 = time.perf_counter()
@@ -410,10 +436,9 @@ def main():
         extra = extras(arrowhead, W, dev, stream, flush, args)
 
     if rank == 0:
-        name = {P64: "fp64", P32: "fp32_bracket"}
         variants = {}
-        for prec, tot, inf in ((primary, total_ms, infos), (other, total_o, infos_o)):
-            variants[name[prec]] = {
+        for form, (tot, inf, _) in runs.items():
+            variants[form] = {
                 "value": world * n * args.steps / (tot / 1e3), "ms_per_step": tot / args.steps,
                 "ms_eig": float(np.mean([x["ms_eig"] for x in inf])),
                 "fp64_steps_per_eigenpair": inf[-1]["total_iter"] / n,
@@ -423,7 +448,7 @@ def main():
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"graded arrowhead n={n}: all eigenpairs + full V",
-                           "n": n, "precision": name[primary],
+                           "n": n, "form": primary,
                            "l2": "512 MiB write between steps (L2 flush)",
                            "parallelism": f"{world} independent instances"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,

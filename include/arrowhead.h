@@ -51,6 +51,10 @@ extern "C" {
 #define AE_FP64 0             /* all-FP64 bisection from the Gershgorin bracket */
 #define AE_FP32_BRACKET 1     /* FP32 opening bracket, verified and finished in FP64 */
 
+/* how the FP64 finish locates the zero (see ae_opts.finish) */
+#define AE_FINISH_BISECT 0    /* bisection, Algorithm 3 (default) */
+#define AE_FINISH_NEWTON 1    /* bracketed Newton on the same function, same stop test */
+
 /* per-eigenpair flag bits reported through ae_diag.flags */
 #define AE_FLAG_DEFLATED 1    /* deflated by the reduction (zero spike / equal pole) */
 #define AE_FLAG_NEARZERO 2    /* recomputed from A^{-1} (Remark 1) */
@@ -67,6 +71,13 @@ typedef struct ae_opts {
     int fixup;         /* 1 (default): Remarks 1 and 2; 0: Algorithm 1 only */
     int profile;       /* 1: time the phases with CUDA events recorded on the
                           call's stream; the times land in ae_info (default 0) */
+    int finish;        /* AE_FINISH_BISECT (default) or AE_FINISH_NEWTON.  Newton
+                          keeps a sign-change bracket of the same Pick function,
+                          every trial point inside it, and Algorithm 3's stop test
+                          (right - left <= 2 eps |mid|, nu = right); it falls back
+                          to bisection when a step leaves the bracket or after 12
+                          steps.  Not in the paper: a faster finish to the same
+                          tolerance.  DPR1-shift remedies always bisect. */
 } ae_opts;
 
 /* Summary counters, filled on the host when passed (forces a stream sync). */
@@ -78,8 +89,8 @@ typedef struct ae_info {
     int n_dpr1shift;      /* Remark 2(b) recomputations */
     int n_capped;         /* eigenpairs that hit max_iter */
     int n_fp32_fallback;  /* FP32 brackets rejected by the FP64 check */
-    int max_iter_used;    /* largest bisection count of any eigenpair */
-    long long total_iter; /* sum of bisection counts (FP64 evaluations) */
+    int max_iter_used;    /* largest FP64 step count (bisection or Newton) of any eigenpair */
+    long long total_iter; /* sum of FP64 step counts (FP64 evaluations of the zero finder) */
     long long fix_iter;   /* the part of total_iter spent in remedies */
     double max_Kb;        /* largest K_b of Eq. (K2) met */
     double max_Knu;       /* largest K_nu of Eq. (K0) met (before remedies) */

@@ -24,6 +24,8 @@ AE_ERR_INPUT = 1002
 AE_ERR_NOCONV = 1003
 AE_FP64 = 0
 AE_FP32_BRACKET = 1
+AE_FINISH_BISECT = 0
+AE_FINISH_NEWTON = 1
 FLAG_DEFLATED, FLAG_NEARZERO, FLAG_OTHERPOLE, FLAG_DPR1SHIFT = 1, 2, 4, 8
 FLAG_CAPPED, FLAG_SINGULAR, FLAG_FP32_FALLBACK = 16, 32, 64
 
@@ -43,7 +45,7 @@ AE_ERR_TOO_LARGE = 1004
 class AeOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("knu_max", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("fixup", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("finish", ctypes.c_int)]
 
 
 class AeInfo(ctypes.Structure):

@@ -32,18 +32,6 @@ void keep_pool_warm() {
     if (dev < 31) done_mask |= 1 << dev;
 }
 
-int resolve_opts(const ae_opts *o, ae::RunOpts &ro) {
-    ae_opts def;
-    ae_default_opts(&def);
-    if (!o) o = &def;
-    if (o->precision != AE_FP64 && o->precision != AE_FP32_BRACKET) return 1;
-    ro.precision = o->precision;
-    ro.knu_max = o->knu_max > 0.0 ? o->knu_max : def.knu_max;
-    ro.max_iter = o->max_iter > 0 ? o->max_iter : def.max_iter;
-    ro.fixup = o->fixup ? 1 : 0;
-    for (int i = 0; i < 5; ++i) ro.ev[i] = nullptr;
-    return 0;
-}
 
 // events for opts->profile; destroyed after the synchronising summary
 struct Prof {
@@ -74,6 +62,21 @@ double bits_to_double(unsigned long long u) {
 
 namespace ae {
 void record_cuda_error(cudaError_t e) { cuda_fail(e); }
+
+int resolve_opts(const ae_opts *o, RunOpts &ro) {
+    ae_opts def;
+    ae_default_opts(&def);
+    if (!o) o = &def;
+    if (o->precision != AE_FP64 && o->precision != AE_FP32_BRACKET) return 1;
+    if (o->finish != AE_FINISH_BISECT && o->finish != AE_FINISH_NEWTON) return 1;
+    ro.precision = o->precision;
+    ro.finish = o->finish;
+    ro.knu_max = o->knu_max > 0.0 ? o->knu_max : def.knu_max;
+    ro.max_iter = o->max_iter > 0 ? o->max_iter : def.max_iter;
+    ro.fixup = o->fixup ? 1 : 0;
+    for (int i = 0; i < 5; ++i) ro.ev[i] = nullptr;
+    return 0;
+}
 }  // namespace ae
 
 extern "C" {
@@ -85,6 +88,7 @@ void ae_default_opts(ae_opts *opts) {
     opts->max_iter = 2200;
     opts->fixup = 1;
     opts->profile = 0;
+    opts->finish = AE_FINISH_BISECT;
 }
 
 const char *ae_status_string(int status) {
@@ -110,7 +114,7 @@ static int solve_common(ae::Kind kind, int n, const double *d, const double *z, 
                         double rho, const ae::Outputs &out, const ae_opts *opts, ae_info *info,
                         void *stream) {
     ae::RunOpts ro;
-    if (resolve_opts(opts, ro)) return -10;
+    if (ae::resolve_opts(opts, ro)) return -10;
     cudaStream_t st = (cudaStream_t)stream;
     keep_pool_warm();
     Prof prof;

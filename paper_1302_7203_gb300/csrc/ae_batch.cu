@@ -157,7 +157,7 @@ __device__ __forceinline__ void batch_unit(const BatchInst &B, long long unit_in
     const int k = (int)(unit_in_inst * EPW) + g;
     const auto R = PolesOf<KIND_ARROW>::make(B.S, m);
     double2 *tb = buf ? buf + g * stride : nullptr;
-    if (W == 32) {
+    if constexpr (W == 32) {
         if (k <= m) eig_item<KIND_ARROW>(R, WarpTeam{lane}, B.S, k, o, tb);
     } else {
         const unsigned mask = ((1u << W) - 1u) << (lane & ~(W - 1));
@@ -414,7 +414,7 @@ static cudaError_t build_plan(Plan *P, int count, const long long *n_off, const 
     P->count = count;
     P->status = status_all;
     P->ro = ro;
-    P->so = SolveOpts{ro.max_iter, ro.precision};
+    P->so = SolveOpts{ro.max_iter, ro.precision, ro.finish};
     std::vector<size_t> soff(count + 1, 0);
     for (int i = 0; i < count; ++i) {
         const int n = (int)(n_off[i + 1] - n_off[i]);
@@ -557,10 +557,8 @@ static cudaError_t time_team(int n, int W, float *ms, cudaStream_t st) {
     k_gen_uniform<<<(unsigned)((rows + 255) / 256) + 1, 256, 0, st>>>(count, n, d, z, al);
     Plan *P = new Plan();
     RunOpts ro{};
+    resolve_opts(nullptr, ro);
     ro.precision = AE_FP32_BRACKET;
-    ro.knu_max = 10.0;
-    ro.max_iter = 2200;
-    ro.fixup = 1;
     e = build_plan(P, count, n_off.data(), nullptr, d, z, al, lam, nullptr, nullptr, ro, W, st);
     cudaEvent_t a = nullptr, b = nullptr;
     if (!e) e = cudaEventCreate(&a);
@@ -599,18 +597,7 @@ int batch_args(int count, const long long *n_off, const double *d_all, const dou
     return 0;
 }
 
-int resolve(const ae_opts *o, ae::RunOpts &ro) {
-    ae_opts def;
-    ae_default_opts(&def);
-    if (!o) o = &def;
-    if (o->precision != AE_FP64 && o->precision != AE_FP32_BRACKET) return 1;
-    ro.precision = o->precision;
-    ro.knu_max = o->knu_max > 0.0 ? o->knu_max : def.knu_max;
-    ro.max_iter = o->max_iter > 0 ? o->max_iter : def.max_iter;
-    ro.fixup = o->fixup ? 1 : 0;
-    for (int i = 0; i < 5; ++i) ro.ev[i] = nullptr;
-    return 0;
-}
+int resolve(const ae_opts *o, ae::RunOpts &ro) { return ae::resolve_opts(o, ro); }
 
 int fail(cudaError_t e) {
     ae::record_cuda_error(e);

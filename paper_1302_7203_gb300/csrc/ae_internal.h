@@ -82,8 +82,12 @@ struct RunOpts {
     double knu_max;
     int max_iter;
     int fixup;
+    int finish;
     cudaEvent_t ev[5];   // phase boundaries when profiling (else null)
 };
+
+// Validate *o (null: the defaults) into ro; nonzero when a field is out of range.
+int resolve_opts(const ae_opts *o, RunOpts &ro);
 
 size_t arrow_scratch_bytes(int n);
 // warps of the eigenvalue kernel for order n (the stored-pair buffer holds one

@@ -60,16 +60,8 @@ extern "C" int arrow_eig_noalloc(int n, const double *d, const double *z, double
     if (!lambda) return -5;
     if (V && ldv < n) return -7;
     if (ae::arrow_scratch_bytes(n) > (size_t)AE_NOALLOC_SCRATCH_BYTES) return AE_ERR_TOO_LARGE;
-    ae_opts def;
-    ae_default_opts(&def);
-    const ae_opts *o = opts ? opts : &def;
-    if (o->precision != AE_FP64 && o->precision != AE_FP32_BRACKET) return -10;
     ae::RunOpts ro;
-    ro.precision = o->precision;
-    ro.knu_max = o->knu_max > 0.0 ? o->knu_max : def.knu_max;
-    ro.max_iter = o->max_iter > 0 ? o->max_iter : def.max_iter;
-    ro.fixup = o->fixup ? 1 : 0;
-    for (int i = 0; i < 5; ++i) ro.ev[i] = nullptr;   // opts->profile is ignored here
+    if (ae::resolve_opts(opts, ro)) return -10;      // opts->profile is ignored here
     cudaStream_t st = (cudaStream_t)stream;
     void *base = nullptr;
     cudaError_t e = scratch_address(&base);

@@ -202,20 +202,14 @@ int ae_serve_create(ae_server **srv, size_t hbm_budget_bytes, int max_inflight, 
     *srv = nullptr;
     if (max_inflight < 1 || max_inflight > 256) return -3;
     if (queue_cap < 1) return -4;
-    ae_opts def;
-    ae_default_opts(&def);
-    const ae_opts *o = opts ? opts : &def;
-    if (o->precision != AE_FP64 && o->precision != AE_FP32_BRACKET) return -5;
+    ae::RunOpts ro;
+    if (ae::resolve_opts(opts, ro)) return -5;
     ae_server *s = new ae_server();
     cudaGetDevice(&s->dev);
     s->budget = hbm_budget_bytes;
     s->max_inflight = max_inflight;
     s->queue_cap = queue_cap;
-    s->ro.precision = o->precision;
-    s->ro.knu_max = o->knu_max > 0.0 ? o->knu_max : def.knu_max;
-    s->ro.max_iter = o->max_iter > 0 ? o->max_iter : def.max_iter;
-    s->ro.fixup = o->fixup ? 1 : 0;
-    for (int i = 0; i < 5; ++i) s->ro.ev[i] = nullptr;
+    s->ro = ro;
     s->streams.resize(max_inflight);
     s->slot_busy.assign(max_inflight, 0);
     for (auto &st : s->streams) {

@@ -31,6 +31,7 @@ namespace ae {
 struct SolveOpts {
     int max_iter;
     int precision;
+    int finish;     // 0: bisection (Algorithm 3); 1: bracketed Newton
 };
 
 struct EigResult {
@@ -277,6 +278,52 @@ __device__ __forceinline__ double secular_sum_stored(const double2 *buf, int m, 
     return T.sum(acc0 + acc1);
 }
 
+// S(x) and S'(x) = sum_{j != skip} zeta_j^2 / (1 - x delta_j)^2 together, for the
+// Newton finish.  Stored pairs: with r_j = 1/(1 - x delta_j) and q_j = c_j r_j,
+// S = sum q_j and S' = sum q_j (delta_j r_j), since c_j delta_j = zeta_j^2.
+template <class Team>
+__device__ __forceinline__ double2 secular_sum_d_stored(const double2 *buf, int m,
+                                                        const Team &T, double x) {
+    double s0 = 0.0, s1 = 0.0, d0 = 0.0, d1 = 0.0;
+    int j = T.rank;
+    for (; j + Team::size < m; j += 2 * Team::size) {
+        const double2 a = buf[j];
+        const double2 b = buf[j + Team::size];
+        const double ra = rcp(fma(-x, a.x, 1.0));
+        const double rb = rcp(fma(-x, b.x, 1.0));
+        const double qa = a.y * ra, qb = b.y * rb;
+        s0 += qa;
+        s1 += qb;
+        d0 = fma(qa, a.x * ra, d0);
+        d1 = fma(qb, b.x * rb, d1);
+    }
+    if (j < m) {
+        const double2 a = buf[j];
+        const double ra = rcp(fma(-x, a.x, 1.0));
+        const double qa = a.y * ra;
+        s0 += qa;
+        d0 = fma(qa, a.x * ra, d0);
+    }
+    return make_double2(T.sum(s0 + s1), T.sum(d0 + d1));
+}
+
+// The same pair from the poles (no stored buffer): with r_j = 1/(delta_j t_j),
+// the term is q_j = zeta_j^2 r_j and its derivative zeta_j^2/t_j^2 = q_j (delta_j r_j) delta_j.
+template <class P, class Team>
+__device__ __forceinline__ double2 secular_sum_d(const P &R, const Team &T, double shift,
+                                                 int skip, double x) {
+    double s0 = 0.0, d0 = 0.0;
+    for (int j = T.rank; j < R.m; j += Team::size) {
+        if (j == skip) continue;
+        const double dj = R.shifted(j, shift, skip);
+        const double r = rcp(dj * fma(-x, dj, 1.0));
+        const double q = R.z2(j) * r;
+        s0 += q;
+        d0 = fma(q * (dj * r), dj, d0);
+    }
+    return make_double2(T.sum(s0), T.sum(d0));
+}
+
 // FP32 analogue on scaled data:
 // T(y) = sum_{j != skip} zz_j / (D_j (1 - y D_j)),  D_j = (p_j - shift) ds sc,
 // zz_j = zeta_j^2 zs.  With x = s y and s = ds sc:  S(x) = s T(y) / zs.
@@ -343,7 +390,9 @@ struct PassA {
     double usq;         // sum zeta_j^2 / delta_j^2
 };
 
-template <class P, class Team>
+// GERSH = false skips the Gershgorin quantities (pmax, pmin, up, lo, wsum),
+// which the Newton finish does not use.
+template <bool GERSH = true, class P, class Team>
 __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift, int skip,
                                         double wscale, double2 *buf = nullptr) {
     dd s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
@@ -361,21 +410,27 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
         else s2 = dd_add_same(s2, t);
         const double p = rcp(del.hi);
         const double aw = R.zabs(j) * fabs(p);
-        pmax = fmax(pmax, p);
-        pmin = fmin(pmin, p);
-        up = fmax(up, fma(aw, wscale, p));
-        lo = fmin(lo, fma(-aw, wscale, p));
-        wsum += aw;
+        if (GERSH) {
+            pmax = fmax(pmax, p);
+            pmin = fmin(pmin, p);
+            up = fmax(up, fma(aw, wscale, p));
+            lo = fmin(lo, fma(-aw, wscale, p));
+            wsum += aw;
+        }
         usq = fma(aw, aw, usq);
     }
     s1 = T.sum(s1);
     s2 = T.sum(s2);
     PassA A;
-    A.pmax = T.max(pmax);
-    A.pmin = T.min(pmin);
-    A.up = T.max(up);
-    A.lo = T.min(lo);
-    A.wsum = T.sum(wsum);
+    if (GERSH) {
+        A.pmax = T.max(pmax);
+        A.pmin = T.min(pmin);
+        A.up = T.max(up);
+        A.lo = T.min(lo);
+        A.wsum = T.sum(wsum);
+    } else {
+        A.pmax = A.pmin = A.up = A.lo = A.wsum = NAN;
+    }
     A.usq = T.sum(usq);
     const dd a = R.a_dd(shift, skip);   // alpha - shift
     if (a.hi < 0.0) {                   // -a > 0: P = -a + S1, Q = -S2
@@ -388,20 +443,36 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
     return A;
 }
 
+// Roots xs <= xb of (B - x)(x - P) + Wq = 0 with Wq > 0 (so xs < min(B, P) and
+// xb > max(B, P)), without cancellation: the root away from zero by the
+// formula, the other from the product of the roots, B P - Wq.
+__device__ __forceinline__ void quad_roots(double B, double P, double Wq, double &xs,
+                                           double &xb) {
+    const double sq = hypot(B - P, 2.0 * sqrt(Wq));
+    const double s = B + P;
+    if (s >= 0.0) {
+        xb = 0.5 * (s + sq);
+        xs = (B * P - Wq) / xb;
+    } else {
+        xs = 0.5 * (s - sq);
+        xb = (B * P - Wq) / xs;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // FP32 opening bracket
 // ---------------------------------------------------------------------------
 // Narrow [left, right] (which holds the zero of a function Phi) with FP32
-// bisection, then verify the new ends in FP64.  Phi(x) = G(x) - K T(y), x = s y,
-// where G is the FP64 part (shift, b, the 1/x term) and T the FP32 sum,
-// K = K_over_s * s / zs.  `dir` = +1 when Phi > 0 below the zero, -1 when
-// above.  Each end is checked with one FP64 evaluation; an end that fails is
-// moved out by 16x its distance (twice at most) and otherwise left where it
-// was.  Returns false when the FP32 data cannot represent the problem or an
-// end had to be given up.
-template <class P, class Team, class G64, class F64>
-__device__ bool fp32_bracket(const P &R, const Team &T, double shift, int skip, double K_over_s,
-                             int dir, G64 g64, F64 f64, double &left, double &right) {
+// bisection into [l, r].  Phi(x) = G(x) - K T(y), x = s y, where G is the FP64
+// part (shift, b, the 1/x term) and T the FP32 sum, K = K_over_s * s / zs.
+// `dir` = +1 when Phi > 0 below the zero, -1 when above.  Returns false when
+// the FP32 data cannot represent the problem ([l, r] is then [left, right]).
+// The new ends are NOT verified here.
+template <class P, class Team, class G64>
+__device__ bool fp32_narrow(const P &R, const Team &T, double shift, int skip, double K_over_s,
+                            int dir, G64 g64, double left, double right, double &l, double &r) {
+    l = left;
+    r = right;
     const double big = fmax(fabs(left), fabs(right));
     if (!(big > 0.0) || !isfinite(big)) return false;
     const double s = ldexp(1.0, ilogb(big));          // x = s y, |y| <= 2
@@ -412,7 +483,6 @@ __device__ bool fp32_bracket(const P &R, const Team &T, double shift, int skip, 
     if (!isfinite(sh)) return false;
     const float sc = (float)scd;
     const double K = K_over_s * s / R.zs;
-    double l = left, r = right;
     for (int it = 0; it < 80; ++it) {
         const double mid = 0.5 * (l + r);
         if (r - l <= 0x1p-21 * fabs(mid)) break;
@@ -426,6 +496,15 @@ __device__ bool fp32_bracket(const P &R, const Team &T, double shift, int skip, 
         if ((phi > 0.0) == (dir > 0)) l = x;
         else r = x;
     }
+    return true;
+}
+
+// Check the narrowed ends [l, r] of a bracket [left, right] in FP64 and move
+// [left, right] in to them.  Each end gets one FP64 evaluation; an end that
+// fails is moved out by 16x the width (twice at most) and otherwise left where
+// it was.  Returns false when an end had to be given up.
+template <class F64>
+__device__ bool fp32_verify(int dir, F64 f64, double l, double r, double &left, double &right) {
     const double w = r - l;
     bool ok = true;
     // left end: Phi must say "below the zero"
@@ -458,6 +537,106 @@ __device__ bool fp32_bracket(const P &R, const Team &T, double shift, int skip, 
 }
 
 // ---------------------------------------------------------------------------
+// Bracketed Newton finish (not in the paper; a faster way to Algorithm 3's
+// answer).  F is strictly decreasing on the bracket (F' <= -1) and has one
+// curvature sign there: convex when the zero lies right of all of F's poles
+// (side > 0), concave when left of them.  `pole` is F's pole nearest the
+// bracket (its largest pole for side > 0, smallest for side < 0).
+// [left, right] holds the zero; gl <= left, right <= gr are known-good ends.
+// Every trial point lies strictly inside the current bracket, each evaluation
+// moves the end on its side (F > 0: left) exactly as bisection does, and the
+// loop stops on Algorithm 3's test right - left <= 2 eps |mid|, so nu = right
+// is the right end of a bracket of the computed F of bisection's final width.
+// Trial points, in order of preference:
+//  * after a step that was lengthened to tol and did not change sides, F is
+//    rounding noise there: one jump of twice the estimated noise width
+//    (err / |F'|) towards the zero, then midpoints only;
+//  * the zero of the one-pole model  a + kappa x + beta / (x - pole)  that
+//    matches F and F' at x (kappa = -1 for the shifted inverse's Pick
+//    function, 0 for the DPR1 secular function): the Newton step of a function
+//    dominated by its nearest pole, exact for a 2 x 2 arrowhead;
+//    lengthened to tol = 2^-52 |x| when shorter (which closes the bracket from
+//    the other side once the zero is that near);
+//  * when that leaves the bracket, the last such point taken from the side
+//    whose steps do not overshoot (F > 0 for side > 0), else the midpoint.
+// Ends lv / rv not yet evaluated in FP64 (from the FP32 phase) are checked
+// after the loop; a failed check is itself a good end on the other side, and
+// the search resumes from the known-good end.  Returns the number of FP64
+// evaluations; `fell_back` reports a failed check.
+// ---------------------------------------------------------------------------
+template <class FD>
+__device__ __forceinline__ int newton_finish(FD fd, int side, double pole, double kappa,
+                                             double gl, double gr, bool lv, bool rv,
+                                             int max_iter, double &left, double &right,
+                                             bool &fell_back) {
+    int it = 0;
+    fell_back = false;
+    for (;;) {
+        double x = 0.5 * (left + right);
+        double pend = NAN;          // last model point from the good side
+        bool nudged = false, noisy = false, pside = false;
+        while (right - left > TWO_EPS * fabs(0.5 * (left + right)) && it < max_iter) {
+            double dF, err;
+            const double F = fd(x, dF, err);
+            ++it;
+            const bool pos = F > 0.0;
+            if (pos) { left = x; lv = true; }
+            else { right = x; rv = true; }
+            const double mid = 0.5 * (left + right);
+            const double towards = pos ? 1.0 : -1.0;    // direction of the zero from x
+            const double tol = 0x1p-52 * fabs(x);
+            double xn;
+            bool nudge = false;
+            if (noisy) {
+                xn = mid;
+            } else if (nudged && pos == pside) {        // the lengthened step stayed on one side
+                noisy = true;
+                xn = x + towards * fmax(2.0 * err / fabs(dF), 2.0 * tol);
+            } else {
+                // one-pole model a + kappa x + beta / (x - pole) through (x, F, F'):
+                // beta = (kappa - F') (x - pole)^2 >= 0
+                const double d0 = fabs(x - pole);
+                const double beta = (kappa - dF) * d0 * d0;
+                const double a = F - kappa * x + (side > 0 ? -beta : beta) / d0;
+                if (kappa == 0.0) {
+                    xn = pole - beta / a;
+                } else {                                 // kappa = -1
+                    double xs, xb;
+                    quad_roots(a, pole, beta, xs, xb);
+                    xn = side > 0 ? xb : xs;
+                }
+                if (fabs(xn - x) < tol) {
+                    xn = x + towards * tol;
+                    nudge = true;
+                } else if (pos == (side > 0)) {
+                    pend = xn;
+                }
+            }
+            if (!(xn > left && xn < right)) {
+                nudge = false;
+                xn = (!noisy && pend > left && pend < right) ? pend : mid;
+            }
+            nudged = nudge;
+            pside = pos;
+            x = xn;
+        }
+        if (lv && rv) break;
+        double dF, err;
+        if (!lv) {
+            ++it;
+            if (fd(left, dF, err) > 0.0) lv = true;
+            else { right = left; left = gl; lv = rv = true; fell_back = true; }
+        }
+        if (!rv) {
+            ++it;
+            if (!(fd(right, dF, err) > 0.0)) rv = true;
+            else { left = right; right = gr; lv = rv = true; fell_back = true; }
+        }
+    }
+    return it;
+}
+
+// ---------------------------------------------------------------------------
 // Algorithm 2 + 3 for the shift pole i on `side`, then lambda = sigma + 1/nu.
 // ---------------------------------------------------------------------------
 template <class P, class Team>
@@ -469,23 +648,14 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
     const double zi = R.zabs(i);
     const double wz = 1.0 / zi;         // w_zeta
     const double c = wz * wz;           // 1/zeta_i^2
-    const PassA A = pass_a(R, T, sigma, i, wz, buf);
+    const bool newton = o.finish == 1;
+    const PassA A = newton ? pass_a<false>(R, T, sigma, i, wz, buf)
+                           : pass_a<true>(R, T, sigma, i, wz, buf);
     // b = (P - Q) / zeta_i^2 in double-double (Theorem 6), rounded once
     const dd num = dd_add(A.P, dd_neg(A.Q));
     const double b = dd_div(num, two_prod(zi, zi)).hi;
     res.Kb = (A.P.hi + A.Q.hi) / fabs(num.hi);
     res.b = b;
-    // Gershgorin bracket of Algorithm 3 for the inverse: diagonal {1/delta_j, 0},
-    // spikes {w_j, w_zeta}, corner b.
-    const double norm1 = fma(A.wsum, wz, wz);
-    double left, right;
-    if (side > 0) {
-        left = fmax(A.pmax, 0.0);
-        right = fmax(fmax(A.up, wz), b + norm1);
-    } else {
-        right = fmin(A.pmin, 0.0);
-        left = fmin(fmin(A.lo, -wz), b - norm1);
-    }
     // with a buffer, each term is c_j / (1 - x delta_j) from the stored pair
     // (5 FP64 instructions instead of 7); the value is the same S(x)
     auto F64 = [&](double x) {
@@ -493,19 +663,102 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                              : secular_sum(R, T, sigma, i, x);
         return (b - x) - c * (S - rcp(x));
     };
-    if (o.precision == 1 && R.has_f32()) {
-        // F = (b - x) + c/x - c S(x),  c S(x) = (c s / zs) T(y)
-        auto G = [&](double x) { return (b - x) + c * rcp(x); };
-        if (!fp32_bracket(R, T, sigma, i, c, +1, G, F64, left, right)) res.flags |= 64;
-    }
+    // F = (b - x) + c/x - c S(x),  c S(x) = (c s / zs) T(y) in the FP32 phase
+    auto G = [&](double x) { return (b - x) + c * rcp(x); };
+    const bool f32 = o.precision == 1 && R.has_f32();
+    double left, right;
     int it = 0;
-    double mid = 0.5 * (left + right);
-    while (right - left > TWO_EPS * fabs(mid) && it < o.max_iter) {
-        const double F = F64(mid);
-        if (F > 0.0) left = mid;
-        else right = mid;
-        mid = 0.5 * (left + right);
-        ++it;
+    if (newton) {
+        // F's poles are 1/delta_j (j != i) and 0; the one nearest the searched
+        // side is 1/delta_{i-1} (side > 0, i > 0) or 1/delta_{i+1} (side < 0,
+        // i < m-1), else 0.  For x beyond all poles F(x) = b - x + sum_k W_k/(x - p_k)
+        // (side > 0), W_k > 0 with sum W = c (sum_j zeta_j^2/delta_j^2 + 1); moving
+        // all weight onto the nearest pole bounds F from one side and keeping
+        // only that pole's weight from the other, so the zeros of the two
+        // one-pole quadratics bracket the zero of F (widened by 2^-30 relative
+        // for the rounding of the weights).
+        const int jn = side > 0 ? i - 1 : i + 1;
+        double pole = 0.0, Wn = c;
+        if (jn >= 0 && jn < R.m) {
+            const double pn = rcp(R.shifted_dd(jn, sigma, i).hi);
+            if (side > 0 ? pn > 0.0 : pn < 0.0) {
+                pole = pn;
+                Wn = c * R.z2(jn) * pn * pn;
+            }
+        }
+        double xs, xb, ys, yb;
+        quad_roots(b, pole, c * (A.usq + 1.0), xs, xb);
+        quad_roots(b, pole, Wn, ys, yb);
+        if (side > 0) {
+            left = fmax(pole, yb - 0x1p-30 * fabs(yb));
+            right = xb + 0x1p-30 * fabs(xb);
+        } else {
+            left = xs - 0x1p-30 * fabs(xs);
+            right = fmin(pole, ys + 0x1p-30 * fabs(ys));
+        }
+        if (!(isfinite(left) && isfinite(right) && left < right)) {
+            // out of range for the quadratic bounds: Gershgorin, as bisection uses
+            const PassA Gb = pass_a<true>(R, T, sigma, i, wz);
+            const double norm1 = fma(Gb.wsum, wz, wz);
+            if (side > 0) {
+                left = fmax(Gb.pmax, 0.0);
+                right = fmax(fmax(Gb.up, wz), b + norm1);
+            } else {
+                right = fmin(Gb.pmin, 0.0);
+                left = fmin(fmin(Gb.lo, -wz), b - norm1);
+            }
+        }
+        // F and F' = -1 - c (S'(x) + 1/x^2) in one pass, and a bound on the
+        // rounding error of F (the terms of S share one sign on this side)
+        auto FD = [&](double x, double &dF, double &err) {
+            const double2 S = buf ? secular_sum_d_stored(buf, R.m, T, x)
+                                  : secular_sum_d(R, T, sigma, i, x);
+            const double rx = rcp(x);
+            dF = -1.0 - c * fma(rx, rx, S.y);
+            err = 0x1p-52 * (fabs(b) + fabs(x) + c * (fabs(S.x) + fabs(rx)));
+            return (b - x) - c * (S.x - rx);
+        };
+        const double gl = left, gr = right;
+        bool lv = true, rv = true;
+        if (f32) {
+            double l, r;
+            if (fp32_narrow(R, T, sigma, i, c, +1, G, left, right, l, r)) {
+                lv = !(l > left);
+                rv = !(r < right);
+                left = l;
+                right = r;
+            } else {
+                res.flags |= 64;
+            }
+        }
+        bool fb;
+        it = newton_finish(FD, side, pole, -1.0, gl, gr, lv, rv, o.max_iter, left, right, fb);
+        if (fb) res.flags |= 64;
+    } else {
+        // Gershgorin bracket of Algorithm 3 for the inverse: diagonal {1/delta_j, 0},
+        // spikes {w_j, w_zeta}, corner b.
+        const double norm1 = fma(A.wsum, wz, wz);
+        if (side > 0) {
+            left = fmax(A.pmax, 0.0);
+            right = fmax(fmax(A.up, wz), b + norm1);
+        } else {
+            right = fmin(A.pmin, 0.0);
+            left = fmin(fmin(A.lo, -wz), b - norm1);
+        }
+        if (f32) {
+            double l, r;
+            if (!fp32_narrow(R, T, sigma, i, c, +1, G, left, right, l, r) ||
+                !fp32_verify(+1, F64, l, r, left, right))
+                res.flags |= 64;
+        }
+        double mid = 0.5 * (left + right);
+        while (right - left > TWO_EPS * fabs(mid) && it < o.max_iter) {
+            const double F = F64(mid);
+            if (F > 0.0) left = mid;
+            else right = mid;
+            mid = 0.5 * (left + right);
+            ++it;
+        }
     }
     const double nu = right;            // Algorithm 3 returns the right end
     res.sigma = sigma;
@@ -563,13 +816,32 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
     // is far outside what a power-of-two rescaled FP32 copy can represent, and
     // these solves are a few per cent of all eigenpairs)
     int it = 0;
-    double mid = 0.5 * (left + right);
-    while (right - left > TWO_EPS * fabs(mid) && it < o.max_iter) {
-        const double phi = PHI(mid);
-        if ((phi > 0.0) == (dir > 0)) left = mid;
-        else right = mid;
-        mid = 0.5 * (left + right);
-        ++it;
+    if (o.finish == 1) {
+        // the Newton finish on dir * phi, which decreases through the zero; the
+        // zero lies beyond all poles {1/delta_j, 0} on the side sign(rho), where
+        // phi is concave (rho > 0) or convex (rho < 0)
+        const int side = rho > 0.0 ? +1 : -1;
+        const double pole = rho > 0.0 ? left : right;
+        const double sg = (double)dir;
+        auto FD = [&](double x, double &dF, double &err) {
+            const double2 S = secular_sum_d(R, T, shift, -1, x);
+            const double rx = rcp(x);
+            dF = sg * rho * fma(rx, rx, S.y);
+            err = 0x1p-52 * (1.0 + fabs(rho) * (fabs(S.x) + fabs(rx)));
+            return sg * fma(rho, S.x - rx, 1.0);
+        };
+        bool fb;
+        it = newton_finish(FD, side, pole, 0.0, left, right, true, true, o.max_iter, left, right,
+                           fb);
+    } else {
+        double mid = 0.5 * (left + right);
+        while (right - left > TWO_EPS * fabs(mid) && it < o.max_iter) {
+            const double phi = PHI(mid);
+            if ((phi > 0.0) == (dir > 0)) left = mid;
+            else right = mid;
+            mid = 0.5 * (left + right);
+            ++it;
+        }
     }
     const double nu = right;
     res.mu = 1.0 / nu;

@@ -1,0 +1,172 @@
+"""GPU parity of the bracketed-Newton finish (ae_opts.finish = AE_FINISH_NEWTON).
+
+The Newton finish searches the same Pick function of the shifted inverse as
+Algorithm 3, keeps a sign-change bracket of it and stops on the same test, so
+its eigenpairs must meet the same bar against the CPU oracle: 10 n eps64 per
+eigenvalue and per vector component.  Covered with and without the FP32
+opening bracket, on the paper's examples, uniform, graded and quantum-dot-like
+spectra, deflation, the DPR1 and SVD wrappers and the batched path; plus exact
+invariances and the evaluation count it exists to cut.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from parity import assert_parity
+from paper_1302_7203_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ae():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1302_7203_gb300 import arrowhead, build
+    build.build()
+    return arrowhead
+
+
+def t(x):
+    return torch.as_tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def opts(ae, precision):
+    return ae.default_opts(precision=precision, finish=ae.AE_FINISH_NEWTON)
+
+
+def solve(ae, d, z, a, o, **kw):
+    r = ae.arrow_eig(t(d), t(z), a, opts=o, info=True, **kw)
+    torch.cuda.synchronize()
+    out = {"lam": r["lam"].cpu().numpy(), "V": r["V"].cpu().numpy(), "info": r["info"]}
+    if "diag" in r:
+        out["diag"] = {k: v.cpu().numpy() for k, v in r["diag"].items()}
+    return out
+
+
+CASES = ["ex1", "ex2", "ex3", "uniform1000", "graded3001", "qdot", "mirrored", "deflation",
+         "n2", "n33"]
+
+
+def case_data(case):
+    if case.startswith("ex"):
+        return W.paper_example(int(case[2]))
+    if case == "uniform1000":
+        return W.uniform_arrow(1000, seed=0)
+    if case == "graded3001":
+        return W.graded_arrow(3001, seed=13)
+    if case == "qdot":
+        return W.quantum_dot_like(2501)
+    if case == "mirrored":
+        return W.mirrored_arrow(41)
+    if case == "n2":
+        return np.array([0.75]), np.array([-0.5]), 2.0
+    if case == "n33":
+        return W.uniform_arrow(33, seed=33)
+    d = np.array([0.5, 3.0, 2.0, 3.0, -1.0, 3.0, 2.0, 7.5, -1.0, 0.25])
+    z = np.array([0.5, -1.0, 0.0, 2.0, 1.0, -0.0, 0.25, -3.0, 0.125, 1.5])
+    return d, z, 0.3
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", CASES)
+def test_newton_parity(ae, case, precision):
+    d, z, a = case_data(case)
+    g = solve(ae, d, z, a, opts(ae, precision))
+    o = oracle.arrow_eig(d, z, a)
+    assert_parity(g["lam"], g["V"], o, len(d) + 1, what=f"newton p={precision} {case}")
+    assert g["info"]["n_capped"] == 0
+
+
+def test_newton_cuts_fp64_evaluations(ae):
+    d, z, a = W.graded_arrow(4000, seed=17)
+    gb = solve(ae, d, z, a, ae.default_opts(precision=1))
+    gn = solve(ae, d, z, a, opts(ae, 1))
+    ib, inn = gb["info"], gn["info"]
+    n_pairs = len(d) + 1
+    # bisection needs ~30 FP64 steps after the FP32 bracket; Newton a handful
+    assert ib["total_iter"] > 25 * n_pairs
+    assert inn["total_iter"] < 6 * n_pairs
+    assert inn["n_fp32_fallback"] <= 0.01 * n_pairs
+
+
+def test_newton_close_to_bisection(ae):
+    # both return the right end of a 2 eps-wide bracket of the same computed
+    # function; away from rounding noise they agree to a few ulps
+    d, z, a = W.uniform_arrow(1500, seed=2)
+    gb = solve(ae, d, z, a, ae.default_opts(precision=1))
+    gn = solve(ae, d, z, a, opts(ae, 1))
+    rel = np.abs(gn["lam"] - gb["lam"]) / np.abs(gb["lam"])
+    assert np.median(rel) <= 2.0 ** -52
+    assert rel.max() <= 10 * len(z) * 2.0 ** -53
+
+
+def test_newton_scale_and_sign_invariance(ae):
+    d, z, a = W.graded_arrow(700, seed=21)
+    o = opts(ae, 1)
+    g0 = solve(ae, d, z, a, o)
+    g2 = solve(ae, d * 2.0 ** 40, z * 2.0 ** 40, a * 2.0 ** 40, o)
+    np.testing.assert_array_equal(g2["lam"], g0["lam"] * 2.0 ** 40)
+    np.testing.assert_array_equal(g2["V"], g0["V"])
+    zs = z.copy()
+    zs[[0, 5, 99]] *= -1
+    g3 = solve(ae, d, zs, a, o)
+    V = g0["V"].copy()
+    V[[0, 5, 99]] *= -1
+    np.testing.assert_array_equal(g3["lam"], g0["lam"])
+    np.testing.assert_array_equal(g3["V"], V)
+
+
+def test_newton_full_size_sampled(ae):
+    n = 16384
+    d, z, a = W.graded_arrow(n, seed=1)
+    g = solve(ae, d, z, a, opts(ae, 1), diag=True)
+    lam, V = g["lam"], g["V"]
+    assert np.all(lam[:-1] >= d) and np.all(d >= lam[1:])
+    np.testing.assert_allclose(np.linalg.norm(V, axis=0), 1.0, atol=4 * n * 2.0 ** -53)
+    flags = g["diag"]["flags"]
+    fixed = np.nonzero(flags & (ae.FLAG_NEARZERO | ae.FLAG_OTHERPOLE | ae.FLAG_DPR1SHIFT))[0]
+    fb = np.nonzero(flags & ae.FLAG_FP32_FALLBACK)[0]
+    rng = np.random.default_rng(9)
+    ks = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1],
+                                   rng.choice(n, 96, replace=False), fixed[:32], fb[:32]]))
+    o = oracle.arrow_eig(d, z, a, ks=ks)
+    assert_parity(lam[ks], V[:, ks], o, n, cols=ks, what="newton graded n=16384 sampled")
+    assert g["info"]["total_iter"] < 6 * n
+
+
+@pytest.mark.parametrize("n", [3, 65, 1000])
+def test_newton_dpr1_and_svd(ae, n):
+    o = opts(ae, 1)
+    d, u, rho = W.uniform_dpr1(n, seed=300 + n)
+    r = ae.dpr1_eig(t(d), t(u), rho, opts=o)
+    torch.cuda.synchronize()
+    ref = oracle.dpr1_eig(d, u, rho)
+    assert_parity(r["lam"].cpu().numpy(), r["Q"].cpu().numpy(),
+                  {"lam": ref["lam"], "abserr": np.zeros(n), "V": ref["Q"]}, n,
+                  what=f"newton dpr1 n={n}")
+    d, z, a = W.uniform_tsvd(n, seed=400 + n)
+    r = ae.tri_arrow_svd(t(d), t(z), a, opts=o)
+    torch.cuda.synchronize()
+    ref = oracle.tsvd(d, z, a)
+    s = r["s"].cpu().numpy()
+    assert_parity(s, r["V"].cpu().numpy(), {"lam": ref["s"], "abserr": np.zeros(n), "V": ref["V"]},
+                  n, what=f"newton svd n={n} (V)")
+    assert_parity(s, r["U"].cpu().numpy(), {"lam": ref["s"], "abserr": np.zeros(n), "V": ref["U"]},
+                  n, what=f"newton svd n={n} (U)")
+
+
+def test_newton_batched(ae):
+    sizes = W.batch_sizes(40, lo=2, hi=900, seed=44)
+    inst = [W.uniform_arrow(int(n), seed=4400 + i) for i, n in enumerate(sizes)]
+    inst.append(W.graded_arrow(500, seed=45))
+    B = ae.Batch(inst, opts=opts(ae, 1))
+    B.run()
+    torch.cuda.synchronize()
+    assert np.all(B.status.cpu().numpy() == 0)
+    for i, (d, z, a) in enumerate(inst):
+        assert_parity(B.lam(i).cpu().numpy(), B.V(i).cpu().numpy(), oracle.arrow_eig(d, z, a),
+                      len(d) + 1, what=f"newton batch instance {i}")
+    B.close()
