@@ -49,6 +49,27 @@ __device__ __forceinline__ dd fast_two_sum(double a, double b) {
     return {s, b - (s - a)};
 }
 
+// TwoSum by magnitude order: FastTwoSum with the larger operand first yields
+// the same exact error term as TwoSum, in three floating-point operations
+// plus one comparison and two selects.
+__device__ __forceinline__ dd two_sum_ord(double a, double b) {
+    const bool o = fabs(a) >= fabs(b);
+    const double x = o ? a : b, y = o ? b : a;
+    const double s = x + y;
+    return {s, y - (s - x)};
+}
+
+// Compensated accumulation of same-sign double-double terms (Sum2 of Ogita,
+// Rump and Oishi, with the error-free TwoSum on the running sum): hi is the
+// plain sum, lo collects the exact rounding errors and the terms' tails.  The
+// caller renormalises every few terms, which keeps |lo| <= k eps |hi| and the
+// result within O(n k eps^2) of the exact sum.
+__device__ __forceinline__ void csum_add(dd &acc, dd t) {
+    const dd s = two_sum_ord(acc.hi, t.hi);
+    acc.hi = s.hi;
+    acc.lo += s.lo + t.lo;
+}
+
 __device__ __forceinline__ dd two_prod(double a, double b) {
     double p = a * b;
     return {p, fma(a, b, -p)};

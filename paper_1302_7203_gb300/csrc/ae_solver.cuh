@@ -138,7 +138,7 @@ struct ArrowPoles {
         return __ldg(pd + j) - shift;
     }
     __device__ __forceinline__ dd shifted_dd(int j, double shift, int) const {
-        return two_sum(__ldg(pd + j), -shift);
+        return two_sum_ord(__ldg(pd + j), -shift);
     }
     __device__ __forceinline__ double z2(int j) const { return __ldg(pz2 + j); }
     __device__ __forceinline__ double zabs(int j) const { return __ldg(pz + j); }
@@ -191,7 +191,7 @@ struct TsvdPoles {
         const double dj = __ldg(pd + j);
         if (i >= 0) {
             const double di = __ldg(pd + i);
-            return dd_mul(two_sum(dj, -di), two_sum(dj, di));
+            return dd_mul(two_sum_ord(dj, -di), two_sum_ord(dj, di));
         }
         return dd_add(two_prod(dj, dj), dd{-shift, 0.0});
     }
@@ -392,33 +392,61 @@ struct PassA {
 
 // GERSH = false skips the Gershgorin quantities (pmax, pmin, up, lo, wsum),
 // which the Newton finish does not use.
+// Each t_j = zeta_j^2 / delta_j is formed as two partial quotients q1 + q2
+// (q1 within an ulp of the quotient, q2 from the FMA residual) and added to
+// its sign's compensated sum (csum_add, renormalised every 16 terms).  With a
+// pole shift (skip >= 0) and poles sorted decreasingly, delta_j > 0 exactly
+// for j < skip, so the two sums come from two branch-free index ranges.  The
+// stored pair is (delta_j, q1).
 template <bool GERSH = true, class P, class Team>
 __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift, int skip,
                                         double wscale, double2 *buf = nullptr) {
     dd s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
+    int c1 = 0, c2 = 0;
     double pmax = -INFINITY, pmin = INFINITY, up = -INFINITY, lo = INFINITY, wsum = 0.0,
            usq = 0.0;
-    for (int j = T.rank; j < R.m; j += Team::size) {
-        if (j == skip) {
-            if (buf) buf[j] = make_double2(0.0, 0.0);
-            continue;
-        }
+    auto term = [&](int j, double &dhi) -> dd {
         const dd del = R.shifted_dd(j, shift, skip);
-        const dd t = dd_div(R.z2_dd(j), del);
-        if (buf) buf[j] = make_double2(del.hi, t.hi);   // (delta_j, zeta_j^2 / delta_j)
-        if (del.hi > 0.0) s1 = dd_add_same(s1, t);
-        else s2 = dd_add_same(s2, t);
+        const dd z2 = R.z2_dd(j);
         const double p = rcp(del.hi);
-        const double aw = R.zabs(j) * fabs(p);
+        const double q1 = z2.hi * p;
+        const double res = fma(-q1, del.lo, fma(-q1, del.hi, z2.hi) + z2.lo);
+        const double q2 = res * p;
+        if (buf) buf[j] = make_double2(del.hi, q1);   // (delta_j, zeta_j^2 / delta_j)
         if (GERSH) {
+            const double aw = R.zabs(j) * fabs(p);
             pmax = fmax(pmax, p);
             pmin = fmin(pmin, p);
             up = fmax(up, fma(aw, wscale, p));
             lo = fmin(lo, fma(-aw, wscale, p));
             wsum += aw;
         }
-        usq = fma(aw, aw, usq);
+        usq = fma(q1, p, usq);                          // zeta_j^2 / delta_j^2
+        dhi = del.hi;
+        return dd{q1, q2};
+    };
+    auto add = [](dd &acc, int &cnt, dd t) {
+        csum_add(acc, t);
+        if (++cnt == 16) {
+            acc = fast_two_sum(acc.hi, acc.lo);
+            cnt = 0;
+        }
+    };
+    double dhi;
+    if (skip >= 0) {
+        for (int j = T.rank; j < skip; j += Team::size) add(s1, c1, term(j, dhi));
+        int j = skip + 1 + ((T.rank - (skip + 1)) % Team::size + Team::size) % Team::size;
+        for (; j < R.m; j += Team::size) add(s2, c2, term(j, dhi));
+        if (buf && skip % Team::size == T.rank) buf[skip] = make_double2(0.0, 0.0);
+    } else {
+        for (int j = T.rank; j < R.m; j += Team::size) {
+            const dd t = term(j, dhi);
+            if (dhi > 0.0) add(s1, c1, t);
+            else add(s2, c2, t);
+        }
     }
+    s1 = fast_two_sum(s1.hi, s1.lo);
+    s2 = fast_two_sum(s2.hi, s2.lo);
     s1 = T.sum(s1);
     s2 = T.sum(s2);
     PassA A;
@@ -575,9 +603,11 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
         double x = 0.5 * (left + right);
         double pend = NAN;          // last model point from the good side
         bool nudged = false, noisy = false, pside = false;
+        double dF = -1.0, err = 0.0;
         while (right - left > TWO_EPS * fabs(0.5 * (left + right)) && it < max_iter) {
-            double dF, err;
-            const double F = fd(x, dF, err);
+            // after a step lengthened to tol the bracket either closes or F is
+            // noise there: F' is not needed (the previous one serves)
+            const double F = fd(x, !nudged, dF, err);
             ++it;
             const bool pos = F > 0.0;
             if (pos) { left = x; lv = true; }
@@ -621,15 +651,14 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
             x = xn;
         }
         if (lv && rv) break;
-        double dF, err;
         if (!lv) {
             ++it;
-            if (fd(left, dF, err) > 0.0) lv = true;
+            if (fd(left, false, dF, err) > 0.0) lv = true;
             else { right = left; left = gl; lv = rv = true; fell_back = true; }
         }
         if (!rv) {
             ++it;
-            if (!(fd(right, dF, err) > 0.0)) rv = true;
+            if (!(fd(right, false, dF, err) > 0.0)) rv = true;
             else { left = right; right = gr; lv = rv = true; fell_back = true; }
         }
     }
@@ -710,11 +739,16 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
         }
         // F and F' = -1 - c (S'(x) + 1/x^2) in one pass, and a bound on the
         // rounding error of F (the terms of S share one sign on this side)
-        auto FD = [&](double x, double &dF, double &err) {
-            const double2 S = buf ? secular_sum_d_stored(buf, R.m, T, x)
-                                  : secular_sum_d(R, T, sigma, i, x);
+        auto FD = [&](double x, bool need_d, double &dF, double &err) {
+            double2 S;
+            if (need_d) {
+                S = buf ? secular_sum_d_stored(buf, R.m, T, x) : secular_sum_d(R, T, sigma, i, x);
+            } else {
+                S.x = buf ? secular_sum_stored(buf, R.m, T, x) : secular_sum(R, T, sigma, i, x);
+                S.y = 0.0;
+            }
             const double rx = rcp(x);
-            dF = -1.0 - c * fma(rx, rx, S.y);
+            if (need_d) dF = -1.0 - c * fma(rx, rx, S.y);
             err = 0x1p-52 * (fabs(b) + fabs(x) + c * (fabs(S.x) + fabs(rx)));
             return (b - x) - c * (S.x - rx);
         };
@@ -823,10 +857,16 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
         const int side = rho > 0.0 ? +1 : -1;
         const double pole = rho > 0.0 ? left : right;
         const double sg = (double)dir;
-        auto FD = [&](double x, double &dF, double &err) {
-            const double2 S = secular_sum_d(R, T, shift, -1, x);
+        auto FD = [&](double x, bool need_d, double &dF, double &err) {
+            double2 S;
+            if (need_d) {
+                S = secular_sum_d(R, T, shift, -1, x);
+            } else {
+                S.x = secular_sum(R, T, shift, -1, x);
+                S.y = 0.0;
+            }
             const double rx = rcp(x);
-            dF = sg * rho * fma(rx, rx, S.y);
+            if (need_d) dF = sg * rho * fma(rx, rx, S.y);
             err = 0x1p-52 * (1.0 + fabs(rho) * (fabs(S.x) + fabs(rx)));
             return sg * fma(rho, S.x - rx, 1.0);
         };
