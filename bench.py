@@ -19,10 +19,11 @@ roofline   the eigenvalue kernel (k_eig): algorithmic FP64 flops per launch
            FP64 ALU peak 152 SMs x 4 flop/clk x 2070 MHz.  Also reported: the
            all-FP64 bisection's algorithmic work over the headline form's k_eig
            time (fp64_bisection_equivalent_tflops).
-forms      fp32 (default headline): FP32 opening bracket, FP64 bisection;
-           fp64: all-FP64 bisection; fp32_newton / fp64_newton: the same with
-           the bracketed Newton finish.  All four are timed; --form picks the
-           headline.
+forms      fp64_newton (default headline): FP64 throughout, the bracketed
+           Newton finish (same Pick function, bracket and stop test as
+           Algorithm 3); fp64: all-FP64 bisection as in Algorithm 3; fp32:
+           FP32 opening bracket then FP64 bisection; fp32_newton.  All four are
+           timed; --form picks the headline.
 cpu_baseline  the CPU oracle on a bounded sample of eigenpairs of the same
            matrix, on all host cores.
 --impl reference   times the CPU oracle alone (the reference arm).
@@ -49,6 +50,28 @@ LAUNCHES_PER_STEP = 8   # k_check k_rank k_reduce k_eig k_fix_decide k_fix_solve
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
 
 
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size k_eig
+# launch (graded n = 16384, fp64_newton form; a 1-pass capture), with the hash
+# of the CUDA sources it was measured on.  The bench reports it as the
+# roofline's traffic only while the form, n and sources match.
+KEIG_TRAFFIC = {"form": "fp64_newton", "n": 16384,
+                "read": 13191656448, "write": 4301616384,
+                "src_sha256": "3edfa919f806ac5e7b79055fe17471d4e2e97959d4b4815e68972ee6be2352c2"}
+
+
+def csrc_sha256():
+    import hashlib
+    d = os.path.join(ROOT, "paper_1302_7203_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        p = os.path.join(d, f)
+        if os.path.isfile(p):
+            h.update(f.encode())
+            with open(p, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
 # solver forms: (ae_opts.precision, ae_opts.finish)
 FORMS = {"fp32": (1, 0), "fp64": (0, 0), "fp32_newton": (1, 1), "fp64_newton": (0, 1)}
 
@@ -56,13 +79,14 @@ FORMS = {"fp32": (1, 0), "fp64": (0, 0), "fp32_newton": (1, 1), "fp64_newton": (
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--form", default="fp32", choices=list(FORMS),
-                   help="headline form: fp32 = FP32 opening bracket + FP64 bisection; "
-                        "fp64 = all-FP64 bisection; *_newton = bracketed Newton finish")
+    p.add_argument("--form", default="fp64_newton", choices=list(FORMS),
+                   help="headline form: fp64_newton = FP64 with the bracketed Newton finish "
+                        "(default); fp32 = FP32 opening bracket + FP64 bisection; fp64 = "
+                        "all-FP64 bisection (Algorithm 3); fp32_newton")
     p.add_argument("--forms", default=",".join(FORMS),
                    help="comma-separated forms to time beside the headline (default: all)")
     p.add_argument("--no-e2e", action="store_true")
@@ -89,7 +113,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -401,8 +425,15 @@ def main():
         i64 = runs["fp64"][1][-1]
         eq = eig_kernel_flops(n, i64["n_reduced"], i64["total_iter"],
                               i64["fix_iter"]) / (eig_ms / 1e3) / 1e12
+    traffic = None
+    if (KEIG_TRAFFIC["form"] == primary and KEIG_TRAFFIC["n"] == n
+            and KEIG_TRAFFIC["src_sha256"] == csrc_sha256()):
+        traffic = KEIG_TRAFFIC["read"] + KEIG_TRAFFIC["write"]
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+            "traffic_note": "bytes per k_eig launch: the per-warp stored (delta_j, "
+                            "zeta_j^2/delta_j) pairs, written once per eigenpair and "
+                            "re-read by each FP64 evaluation",
             "kernel": "k_eig", "kernel_ms": eig_ms,
             "fp64_bisection_equivalent_tflops": eq,
             "peak_note": "FP64 ALU: 152 SMs x 4 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)"}
