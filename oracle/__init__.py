@@ -65,6 +65,10 @@ def _load():
         D = ctypes.c_double
         lib.oracle_arrow_eig.argtypes = [I, P, P, D, P, I, P, P, P, P, P, P, P, P, I]
         lib.oracle_arrow_eig.restype = I
+        lib.oracle_herm_eig.argtypes = [I, P, P, P, D, P, I, P, P, P, P, P, P, P, P, P, I]
+        lib.oracle_herm_eig.restype = I
+        lib.oracle_nsym_eig.argtypes = [I, P, P, P, D, P, I, P, P, P, P, P, P, P, P, P, I]
+        lib.oracle_nsym_eig.restype = I
         lib.oracle_reduce.argtypes = [I, P, P, P, P, P]
         lib.oracle_reduce.restype = I
         lib.oracle_inverse_element.argtypes = [I, P, P, D, I, P, P, P]
@@ -127,6 +131,72 @@ def arrow_eig(d, z, alpha, ks=None, vectors=True, nthreads=0):
         raise ValueError("oracle_arrow_eig: invalid input")
     if vectors:
         out["V"] = V.T.copy()
+    return out
+
+
+def _scalars(nk):
+    return {k: np.zeros(nk) for k in ("lam", "lam_lo", "sigma", "mu_hi", "mu_lo", "relerr",
+                                      "abserr")}
+
+
+def _ks(ks, n):
+    if ks is None:
+        return None, n
+    kk = np.ascontiguousarray(ks, dtype=np.int32)
+    return kk, kk.size
+
+
+def herm_eig(d, z, alpha, ks=None, vectors=True, nthreads=0):
+    """Eigen-decomposition of the Hermitian arrowhead C = [diag(d) z; z^* alpha]
+    (Sec. 6.1), z complex (len(d) entries, the column above the corner).
+
+    Same keys as arrow_eig; ``U`` is complex (n x len(ks)), rows in input order.
+    """
+    lib = _load()
+    d = _f64(d)
+    z = np.asarray(z, dtype=np.complex128)
+    zre, zim = _f64(z.real), _f64(z.imag)
+    n = d.size + 1
+    kk, nk = _ks(ks, n)
+    out = _scalars(nk)
+    Ur = np.zeros((nk, n)) if vectors else None
+    Ui = np.zeros((nk, n)) if vectors else None
+    rc = lib.oracle_herm_eig(n, _ptr(d), _ptr(zre), _ptr(zim), float(alpha), _ptr(kk), nk,
+                             _ptr(out["lam"]), _ptr(out["lam_lo"]), _ptr(out["sigma"]),
+                             _ptr(out["mu_hi"]), _ptr(out["mu_lo"]), _ptr(out["relerr"]),
+                             _ptr(out["abserr"]), _ptr(Ur), _ptr(Ui), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_herm_eig: invalid input")
+    if vectors:
+        out["U"] = (Ur + 1j * Ui).T.copy()
+    return out
+
+
+def nsym_eig(d, zc, zr, alpha, ks=None, vectors=True, nthreads=0):
+    """Eigen-decomposition of the non-symmetric arrowhead G = [diag(d) zc; zr^T alpha]
+    (Remark, Sec. 6.1), zc_r zr_r > 0 or both zero.
+
+    Same keys as arrow_eig; ``X`` right and ``Y`` left eigenvectors (n x len(ks)),
+    scaled so that y_k^T x_k = 1.
+    """
+    lib = _load()
+    d = _f64(d)
+    zc = _f64(zc)
+    zr = _f64(zr)
+    n = d.size + 1
+    kk, nk = _ks(ks, n)
+    out = _scalars(nk)
+    X = np.zeros((nk, n)) if vectors else None
+    Y = np.zeros((nk, n)) if vectors else None
+    rc = lib.oracle_nsym_eig(n, _ptr(d), _ptr(zc), _ptr(zr), float(alpha), _ptr(kk), nk,
+                             _ptr(out["lam"]), _ptr(out["lam_lo"]), _ptr(out["sigma"]),
+                             _ptr(out["mu_hi"]), _ptr(out["mu_lo"]), _ptr(out["relerr"]),
+                             _ptr(out["abserr"]), _ptr(X), _ptr(Y), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_nsym_eig: invalid input")
+    if vectors:
+        out["X"] = X.T.copy()
+        out["Y"] = Y.T.copy()
     return out
 
 

@@ -22,6 +22,10 @@
  *  - DPR1  M = D + rho u u^T (Sec. 6.3): zeros of 1 + rho sum u_j^2/(d_j - l),
  *    vectors q ~ (D - l I)^{-1} u, solved directly (not through the
  *    arrowhead reduction the method uses).
+ *  - Hermitian arrowhead [D z; z^* alpha] (Sec. 6.1) and the non-symmetric
+ *    [D zc; zr^T alpha] (the Remark of Sec. 6.1): zeros of the same Pick
+ *    function with weights |zeta|^2, resp. zc zr, exact in double-double;
+ *    vectors from the rows of (C - l I) u = 0 directly.
  *  - SVD of B = [D z; 0 alpha] (Sec. 6.2): eigen-decomposition of the
  *    arrowhead B^T B = [D^2, D z; z^T D, alpha^2 + z^T z], singular values
  *    sqrt(l), right vectors v, left vectors u_j = s v_j / d_j, u_n = alpha v_n / s.
@@ -143,7 +147,7 @@ typedef struct {
     int *run_pos;    /* per original row (kind 0/2): position in its run */
     int *pole_row;   /* reduced pole j -> original row of its head */
     double *pole_d;  /* reduced pole values, strictly decreasing */
-    dd *pole_z;      /* reduced zeta' > 0 (dd) */
+    dd *pole_c;      /* reduced zeta'^2 = sum of zeta^2 over the run (dd) */
     int *defl_row;   /* deflated rows, in sorted order */
 } reduction;
 
@@ -158,11 +162,14 @@ static int cmp_desc(const void *a, const void *b) {
 
 static void free_reduction(reduction *R) {
     free(R->order); free(R->kind); free(R->run_head); free(R->run_pos);
-    free(R->pole_row); free(R->pole_d); free(R->pole_z); free(R->defl_row);
+    free(R->pole_row); free(R->pole_d); free(R->pole_c); free(R->defl_row);
 }
 
-/* key[] are the pole values used for ordering and equality; z[] the spikes */
-static int reduce(int n1, const double *key, const double *z, reduction *R) {
+/* key[] are the pole values used for ordering and equality; z[] the spikes
+   (|zeta| for the Hermitian and non-symmetric forms).  z2[], when given, are
+   the exact squares zeta_r^2 in double-double (|zeta|^2 of a complex spike,
+   or the product of a non-symmetric pair); else zeta_r^2 = TwoProd(z_r, z_r). */
+static int reduce2(int n1, const double *key, const double *z, const dd *z2, reduction *R) {
     memset(R, 0, sizeof(*R));
     R->n1 = n1;
     int cap = n1 > 0 ? n1 : 1;
@@ -172,14 +179,13 @@ static int reduce(int n1, const double *key, const double *z, reduction *R) {
     R->run_pos = malloc(sizeof(int) * cap);
     R->pole_row = malloc(sizeof(int) * cap);
     R->pole_d = malloc(sizeof(double) * cap);
-    R->pole_z = malloc(sizeof(dd) * cap);
+    R->pole_c = malloc(sizeof(dd) * cap);
     R->defl_row = malloc(sizeof(int) * cap);
     for (int r = 0; r < n1; r++) R->order[r] = r;
     g_sort_key = key;
     qsort(R->order, n1, sizeof(int), cmp_desc);
     int m = 0, nd = 0;
     int last_head = -1;       /* sorted run head (original row) */
-    dd run_sq = dd_from(0.0); /* sum of z^2 over the current run */
     int run_len = 0;
     for (int s = 0; s < n1; s++) {
         int r = R->order[s];
@@ -190,29 +196,32 @@ static int reduce(int n1, const double *key, const double *z, reduction *R) {
             R->defl_row[nd++] = r;
             continue;
         }
+        dd sq = z2 ? z2[r] : two_prod(z[r], z[r]);
         if (last_head >= 0 && key[r] == key[last_head]) {
             R->kind[r] = 2;
             R->run_head[r] = last_head;
             R->run_pos[r] = run_len++;
             R->defl_row[nd++] = r;
-            run_sq = dd_add(run_sq, two_prod(z[r], z[r]));
-            R->pole_z[m - 1] = dd_sqrt(run_sq);
+            R->pole_c[m - 1] = dd_add(R->pole_c[m - 1], sq);
         } else {
             R->kind[r] = 0;
             R->run_head[r] = r;
             R->run_pos[r] = 0;
             run_len = 1;
             last_head = r;
-            run_sq = two_prod(z[r], z[r]);
             R->pole_row[m] = r;
             R->pole_d[m] = key[r];
-            R->pole_z[m] = dd_abs(dd_from(z[r]));
+            R->pole_c[m] = sq;
             m++;
         }
     }
     R->m = m;
     R->ndefl = nd;
     return 0;
+}
+
+static int reduce(int n1, const double *key, const double *z, reduction *R) {
+    return reduce2(n1, key, z, NULL, R);
 }
 
 /* ------------------------------------------------------------------ */
@@ -575,6 +584,138 @@ static void run_vector(const reduction *R, const double *z, int row, int nrows,
 }
 
 /* ------------------------------------------------------------------ */
+/* the zeros of a reduced arrowhead and their output order            */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    reduction R;
+    int n1, ncomp;
+    dd *c;            /* pole weights zeta'_j^2 */
+    zero_info *Z;     /* computed zeros (those wanted) */
+    int *slot;        /* output position -> computed k, or -1 - t for deflated row t */
+} arrow_sol;
+
+static void arrow_sol_free(arrow_sol *A) {
+    free(A->slot); free(A->Z); free(A->c);
+    free_reduction(&A->R);
+}
+
+/* d, zabs: n-1 rows (zabs only decides zero spikes and, without z2, gives the
+   weights); z2: exact zeta^2 (dd) or NULL.  Positions ks[0..nk) (all if NULL). */
+static void arrow_solve(int n, const double *d, const double *zabs, const dd *z2, double alpha,
+                        const int *ks, int nk, int nthreads, arrow_sol *A) {
+    int n1 = n - 1;
+    A->n1 = n1;
+    reduce2(n1, d, zabs, z2, &A->R);
+    int m = A->R.m;
+    A->c = malloc(sizeof(dd) * (m > 0 ? m : 1));
+    for (int j = 0; j < m; j++) A->c[j] = A->R.pole_c[j];
+    int ncomp = m + 1;
+    A->ncomp = ncomp;
+    int all = (ks == NULL);
+    if (all) nk = n;
+    int need_all_comp = all || A->R.ndefl > 0;
+    A->Z = calloc(ncomp, sizeof(zero_info));
+    char *want = calloc(ncomp, 1);
+    if (need_all_comp) {
+        memset(want, 1, ncomp);
+    } else {
+        for (int i = 0; i < nk; i++) want[ks[i]] = 1;
+    }
+    zero_info *Z = A->Z;
+    const dd *c = A->c;
+    const reduction *R = &A->R;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        dd *buf = malloc(sizeof(dd) * (m > 0 ? m : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int k = 0; k < ncomp; k++) {
+            if (!want[k]) continue;
+            if (m == 0) {
+                Z[k].pole = -1; Z[k].sigma = alpha; Z[k].mu = dd_from(0.0);
+                Z[k].relerr = 0.0; Z[k].abserr = 0.0;
+            } else {
+                Z[k] = solve_zero(KIND_ARROW, m, R->pole_d, c, dd_from(alpha), 0.0, k, buf);
+            }
+        }
+        free(buf);
+    }
+    A->slot = malloc(sizeof(int) * n);
+    if (need_all_comp) {
+        double *lam_comp = malloc(sizeof(double) * ncomp);
+        for (int k = 0; k < ncomp; k++) lam_comp[k] = dd_add(dd_from(Z[k].sigma), Z[k].mu).hi;
+        double *lam_defl = malloc(sizeof(double) * (R->ndefl > 0 ? R->ndefl : 1));
+        for (int t = 0; t < R->ndefl; t++) lam_defl[t] = d[R->defl_row[t]];
+        merge_order(ncomp, lam_comp, R->ndefl, lam_defl, A->slot);
+        free(lam_comp); free(lam_defl);
+    } else {
+        for (int i = 0; i < n; i++) A->slot[i] = i;
+    }
+    free(want);
+}
+
+/* the scalar outputs of position `pos` into entry i of the output arrays;
+   returns the computed zero (or NULL for a deflated row, *row set) */
+static const zero_info *arrow_scalars(const arrow_sol *A, const double *d, int pos, int i,
+                                      double *lam, double *lam_lo, double *sigma_out,
+                                      double *mu_hi, double *mu_lo, double *relerr,
+                                      double *abserr, int *row) {
+    int s = A->slot[pos];
+    if (s >= 0) {
+        const zero_info *zi = &A->Z[s];
+        dd l = dd_add(dd_from(zi->sigma), zi->mu);
+        lam[i] = l.hi;
+        if (lam_lo) lam_lo[i] = l.lo;
+        if (sigma_out) sigma_out[i] = zi->sigma;
+        if (mu_hi) mu_hi[i] = zi->mu.hi;
+        if (mu_lo) mu_lo[i] = zi->mu.lo;
+        if (relerr) relerr[i] = zi->relerr;
+        if (abserr) abserr[i] = zi->abserr;
+        return zi;
+    }
+    int t = -1 - s;
+    *row = A->R.defl_row[t];
+    lam[i] = d[*row];
+    if (lam_lo) lam_lo[i] = 0.0;
+    if (sigma_out) sigma_out[i] = d[*row];
+    if (mu_hi) mu_hi[i] = 0.0;
+    if (mu_lo) mu_lo[i] = 0.0;
+    if (relerr) relerr[i] = 0.0;
+    if (abserr) abserr[i] = 0.0;
+    return NULL;
+}
+
+/* the denominators (d_r - sigma) - mu of Eq. (Aeigenvec) in double-double */
+static dd vec_den(const double *d, int r, const zero_info *zi) {
+    return dd_sub(two_sum(d[r], -zi->sigma), zi->mu);
+}
+
+/* the run data of a run-deflated row: Rm1 = |zeta'| of the rows before it,
+   Rm including it (dd), over the exact squares sq() */
+static void run_norms(const reduction *R, const dd *sq, int row, dd *Rm1, dd *Rm, int *s0) {
+    int head = R->run_head[row];
+    int pos = R->run_pos[row];
+    int s = 0;
+    while (R->order[s] != head) s++;
+    *s0 = s;
+    dd prev = dd_from(0.0);
+    int cnt = 0;
+    for (; s < R->n1 && cnt < pos; s++) {
+        int r = R->order[s];
+        if (R->kind[r] == 1) continue;
+        if (R->run_head[r] != head) break;
+        prev = dd_add(prev, sq[r]);
+        cnt++;
+    }
+    *Rm1 = dd_sqrt(prev);
+    *Rm = dd_sqrt(dd_add(prev, sq[row]));
+}
+
+/* ------------------------------------------------------------------ */
 /* public: arrowhead eigen-decomposition                              */
 /* ------------------------------------------------------------------ */
 /*
@@ -595,113 +736,226 @@ int oracle_arrow_eig(int n, const double *d, const double *z, double alpha,
         if (!isfinite(d[r]) || !isfinite(z[r])) return -1;
     if (!isfinite(alpha)) return -1;
     int n1 = n - 1;
-    reduction R;
-    reduce(n1, d, z, &R);
-    int m = R.m;
-    dd *c = malloc(sizeof(dd) * (m > 0 ? m : 1));
-    for (int j = 0; j < m; j++) c[j] = dd_mul(R.pole_z[j], R.pole_z[j]);
-    int ncomp = m + 1;
+    arrow_sol A;
+    arrow_solve(n, d, z, NULL, alpha, ks, nk, nthreads, &A);
     int all = (ks == NULL);
     if (all) nk = n;
-    /* which computed zeros are needed */
-    int need_all_comp = all || R.ndefl > 0;
-    zero_info *Z = calloc(ncomp, sizeof(zero_info));
-    char *want = calloc(ncomp, 1);
-    if (need_all_comp) {
-        memset(want, 1, ncomp);
-    } else {
-        for (int i = 0; i < nk; i++) want[ks[i]] = 1;
-    }
-#ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel
-#endif
-    {
-        dd *buf = malloc(sizeof(dd) * (m > 0 ? m : 1));
-#ifdef _OPENMP
-#pragma omp for schedule(dynamic, 1)
-#endif
-        for (int k = 0; k < ncomp; k++) {
-            if (!want[k]) continue;
-            if (m == 0) {
-                Z[k].pole = -1; Z[k].sigma = alpha; Z[k].mu = dd_from(0.0);
-                Z[k].relerr = 0.0; Z[k].abserr = 0.0;
-            } else {
-                Z[k] = solve_zero(KIND_ARROW, m, R.pole_d, c, dd_from(alpha), 0.0, k, buf);
-            }
-        }
-        free(buf);
-    }
-    /* computed eigenvalues (dd) */
-    double *lam_comp = malloc(sizeof(double) * ncomp);
-    for (int k = 0; k < ncomp; k++) {
-        dd l = dd_add(dd_from(Z[k].sigma), Z[k].mu);
-        lam_comp[k] = l.hi;
-    }
-    double *lam_defl = malloc(sizeof(double) * (R.ndefl > 0 ? R.ndefl : 1));
-    for (int t = 0; t < R.ndefl; t++) lam_defl[t] = d[R.defl_row[t]];
-    int *slot = malloc(sizeof(int) * n);
-    if (need_all_comp) {
-        merge_order(ncomp, lam_comp, R.ndefl, lam_defl, slot);
-    } else {
-        for (int i = 0; i < n; i++) slot[i] = i;
-    }
-    int rc = 0;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int i = 0; i < nk; i++) {
         int pos = all ? i : ks[i];
-        int s = slot[pos];
+        int row = -1;
+        const zero_info *zi = arrow_scalars(&A, d, pos, i, lam, lam_lo, sigma_out, mu_hi,
+                                            mu_lo, relerr, abserr, &row);
         double *col = V ? V + (size_t)i * n : NULL;
-        if (s >= 0) {
-            zero_info *zi = &Z[s];
-            dd l = dd_add(dd_from(zi->sigma), zi->mu);
-            lam[i] = l.hi;
-            if (lam_lo) lam_lo[i] = l.lo;
-            if (sigma_out) sigma_out[i] = zi->sigma;
-            if (mu_hi) mu_hi[i] = zi->mu.hi;
-            if (mu_lo) mu_lo[i] = zi->mu.lo;
-            if (relerr) relerr[i] = zi->relerr;
-            if (abserr) abserr[i] = zi->abserr;
-            if (col) {
-                /* x_r = z_r / ((d_r - sigma) - mu), x_last = -1 */
-                dd *x = malloc(sizeof(dd) * n);
-                dd ss = dd_from(1.0);
-                for (int r = 0; r < n1; r++) {
-                    if (z[r] == 0.0) { x[r] = dd_from(0.0); continue; }
-                    dd den = dd_sub(two_sum(d[r], -zi->sigma), zi->mu);
-                    x[r] = dd_div(dd_from(z[r]), den);
-                    ss = dd_add(ss, dd_mul(x[r], x[r]));
-                }
-                x[n1] = dd_from(-1.0);
-                dd nrm = dd_sqrt(ss);
-                for (int r = 0; r < n; r++) col[r] = dd_div(x[r], nrm).hi;
-                free(x);
+        if (!col) continue;
+        if (zi) {
+            /* x_r = z_r / ((d_r - sigma) - mu), x_last = -1 */
+            dd *x = malloc(sizeof(dd) * n);
+            dd ss = dd_from(1.0);
+            for (int r = 0; r < n1; r++) {
+                if (z[r] == 0.0) { x[r] = dd_from(0.0); continue; }
+                x[r] = dd_div(dd_from(z[r]), vec_den(d, r, zi));
+                ss = dd_add(ss, dd_mul(x[r], x[r]));
             }
+            x[n1] = dd_from(-1.0);
+            dd nrm = dd_sqrt(ss);
+            for (int r = 0; r < n; r++) col[r] = dd_div(x[r], nrm).hi;
+            free(x);
+        } else if (A.R.kind[row] == 1) {
+            for (int r = 0; r < n; r++) col[r] = 0.0;
+            col[row] = 1.0;
         } else {
-            int t = -1 - s;
-            int row = R.defl_row[t];
-            lam[i] = d[row];
-            if (lam_lo) lam_lo[i] = 0.0;
-            if (sigma_out) sigma_out[i] = d[row];
-            if (mu_hi) mu_hi[i] = 0.0;
-            if (mu_lo) mu_lo[i] = 0.0;
-            if (relerr) relerr[i] = 0.0;
-            if (abserr) abserr[i] = 0.0;
-            if (col) {
-                if (R.kind[row] == 1) {
-                    for (int r = 0; r < n; r++) col[r] = 0.0;
-                    col[row] = 1.0;
-                } else {
-                    run_vector(&R, z, row, n, col);
-                }
-            }
+            run_vector(&A.R, z, row, n, col);
         }
     }
-    free(slot); free(lam_defl); free(lam_comp); free(want); free(Z); free(c);
-    free_reduction(&R);
-    return rc;
+    arrow_sol_free(&A);
+    return 0;
+}
+
+/*
+ * Hermitian arrowhead C = [D z; z^* alpha] (Sec. 6.1): z complex, given as
+ * (zre, zim), n-1 entries; the column above the corner holds zeta_r.  The
+ * eigenvalues of C are the zeros of f(l) = alpha - l - sum |zeta_r|^2/(d_r - l),
+ * with |zeta_r|^2 = zre^2 + zim^2 exactly in double-double, and the
+ * eigenvectors u = x/||x||, x_r = zeta_r/(d_r - l), x_n = -1 (C u = l u row by
+ * row).  Deflated rows: e_r for zeta_r = 0; a run of equal d gives the real
+ * Helmert-type vector of the moduli, with each row r scaled by the phase
+ * zeta_r/|zeta_r| (the unitary Phi of Sec. 6.1).  U is column-major n x nk,
+ * real and imaginary parts in Ure, Uim (either pair may be NULL).
+ */
+int oracle_herm_eig(int n, const double *d, const double *zre, const double *zim,
+                    double alpha, const int *ks, int nk, double *lam, double *lam_lo,
+                    double *sigma_out, double *mu_hi, double *mu_lo, double *relerr,
+                    double *abserr, double *Ure, double *Uim, int nthreads) {
+    if (n < 1) return -1;
+    int n1 = n - 1;
+    for (int r = 0; r < n1; r++)
+        if (!isfinite(d[r]) || !isfinite(zre[r]) || !isfinite(zim[r])) return -1;
+    if (!isfinite(alpha)) return -1;
+    double *za = malloc(sizeof(double) * (n1 > 0 ? n1 : 1));
+    dd *z2 = malloc(sizeof(dd) * (n1 > 0 ? n1 : 1));
+    for (int r = 0; r < n1; r++) {
+        z2[r] = dd_add(two_prod(zre[r], zre[r]), two_prod(zim[r], zim[r]));
+        za[r] = dd_sqrt(z2[r]).hi;
+    }
+    arrow_sol A;
+    arrow_solve(n, d, za, z2, alpha, ks, nk, nthreads, &A);
+    int all = (ks == NULL);
+    if (all) nk = n;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int i = 0; i < nk; i++) {
+        int pos = all ? i : ks[i];
+        int row = -1;
+        const zero_info *zi = arrow_scalars(&A, d, pos, i, lam, lam_lo, sigma_out, mu_hi,
+                                            mu_lo, relerr, abserr, &row);
+        if (!Ure || !Uim) continue;
+        double *cr = Ure + (size_t)i * n, *ci = Uim + (size_t)i * n;
+        for (int r = 0; r < n; r++) { cr[r] = 0.0; ci[r] = 0.0; }
+        if (zi) {
+            dd *t = malloc(sizeof(dd) * n);     /* 1/((d_r - sigma) - mu) */
+            dd ss = dd_from(1.0);
+            for (int r = 0; r < n1; r++) {
+                if (za[r] == 0.0) { t[r] = dd_from(0.0); continue; }
+                t[r] = dd_div(dd_from(1.0), vec_den(d, r, zi));
+                ss = dd_add(ss, dd_mul(z2[r], dd_mul(t[r], t[r])));
+            }
+            dd nrm = dd_sqrt(ss);
+            for (int r = 0; r < n1; r++) {
+                dd tr = dd_div(t[r], nrm);
+                cr[r] = dd_mul_d(tr, zre[r]).hi;
+                ci[r] = dd_mul_d(tr, zim[r]).hi;
+            }
+            cr[n1] = dd_div(dd_from(-1.0), nrm).hi;
+            free(t);
+        } else if (A.R.kind[row] == 1) {
+            cr[row] = 1.0;
+        } else {
+            /* Phi times the real run vector of the moduli: rows l before `row`
+               in its run get -|zeta_q| zeta_l / (R_{m-1} R_m), the row itself
+               (zeta_q/|zeta_q|) R_{m-1}/R_m */
+            dd Rm1, Rm;
+            int s0;
+            run_norms(&A.R, z2, row, &Rm1, &Rm, &s0);
+            dd den = dd_mul(Rm1, Rm);
+            dd zq = dd_sqrt(z2[row]);
+            int cnt = 0, head = A.R.run_head[row], p = A.R.run_pos[row];
+            for (int s = s0; s < n1 && cnt < p; s++) {
+                int r = A.R.order[s];
+                if (A.R.kind[r] == 1) continue;
+                if (A.R.run_head[r] != head) break;
+                dd f = dd_neg(dd_div(zq, den));
+                cr[r] = dd_mul_d(f, zre[r]).hi;
+                ci[r] = dd_mul_d(f, zim[r]).hi;
+                cnt++;
+            }
+            dd g = dd_div(Rm1, dd_mul(Rm, zq));
+            cr[row] = dd_mul_d(g, zre[row]).hi;
+            ci[row] = dd_mul_d(g, zim[row]).hi;
+        }
+    }
+    arrow_sol_free(&A);
+    free(za); free(z2);
+    return 0;
+}
+
+/*
+ * Non-symmetric arrowhead G = [D zc; zr^T alpha] (Remark in Sec. 6.1) with
+ * zc_r zr_r > 0, or zc_r = zr_r = 0.  Its eigenvalues are the zeros of
+ * f(l) = alpha - l - sum zc_r zr_r/(d_r - l) (zc_r zr_r exactly in
+ * double-double); right eigenvectors x_r = zc_r/(d_r - l), left
+ * y_r = zr_r/(d_r - l), x_n = y_n = -1 (G x = l x and y^T G = l y^T row by
+ * row), both divided by sqrt(1 + sum zc_r zr_r/(d_r - l)^2) so that
+ * y^T x = 1.  Deflated rows: e_r for both; a run of equal d gives the Helmert-
+ * type vector v of the symmetric arrowhead with zeta_r = sqrt(zc_r zr_r),
+ * mapped by x_r = (zc_r/zeta_r) v_r and y_r = (zr_r/zeta_r) v_r.  X, Y:
+ * column-major n x nk (either may be NULL).  Returns -1 when a pair has
+ * opposite signs or only one zero.
+ */
+int oracle_nsym_eig(int n, const double *d, const double *zc, const double *zr, double alpha,
+                    const int *ks, int nk, double *lam, double *lam_lo, double *sigma_out,
+                    double *mu_hi, double *mu_lo, double *relerr, double *abserr, double *X,
+                    double *Y, int nthreads) {
+    if (n < 1) return -1;
+    int n1 = n - 1;
+    for (int r = 0; r < n1; r++) {
+        if (!isfinite(d[r]) || !isfinite(zc[r]) || !isfinite(zr[r])) return -1;
+        if ((zc[r] == 0.0) != (zr[r] == 0.0)) return -1;
+        if (zc[r] != 0.0 && (zc[r] > 0.0) != (zr[r] > 0.0)) return -1;
+    }
+    if (!isfinite(alpha)) return -1;
+    double *za = malloc(sizeof(double) * (n1 > 0 ? n1 : 1));
+    dd *z2 = malloc(sizeof(dd) * (n1 > 0 ? n1 : 1));
+    for (int r = 0; r < n1; r++) {
+        z2[r] = two_prod(zc[r], zr[r]);
+        za[r] = dd_sqrt(z2[r]).hi;
+    }
+    arrow_sol A;
+    arrow_solve(n, d, za, z2, alpha, ks, nk, nthreads, &A);
+    int all = (ks == NULL);
+    if (all) nk = n;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int i = 0; i < nk; i++) {
+        int pos = all ? i : ks[i];
+        int row = -1;
+        const zero_info *zi = arrow_scalars(&A, d, pos, i, lam, lam_lo, sigma_out, mu_hi,
+                                            mu_lo, relerr, abserr, &row);
+        double *cx = X ? X + (size_t)i * n : NULL, *cy = Y ? Y + (size_t)i * n : NULL;
+        if (!cx && !cy) continue;
+        for (int r = 0; r < n; r++) {
+            if (cx) cx[r] = 0.0;
+            if (cy) cy[r] = 0.0;
+        }
+        if (zi) {
+            dd *t = malloc(sizeof(dd) * n);
+            dd ss = dd_from(1.0);
+            for (int r = 0; r < n1; r++) {
+                if (za[r] == 0.0) { t[r] = dd_from(0.0); continue; }
+                t[r] = dd_div(dd_from(1.0), vec_den(d, r, zi));
+                ss = dd_add(ss, dd_mul(z2[r], dd_mul(t[r], t[r])));
+            }
+            dd nrm = dd_sqrt(ss);
+            for (int r = 0; r < n1; r++) {
+                dd tr = dd_div(t[r], nrm);
+                if (cx) cx[r] = dd_mul_d(tr, zc[r]).hi;
+                if (cy) cy[r] = dd_mul_d(tr, zr[r]).hi;
+            }
+            double last = dd_div(dd_from(-1.0), nrm).hi;
+            if (cx) cx[n1] = last;
+            if (cy) cy[n1] = last;
+            free(t);
+        } else if (A.R.kind[row] == 1) {
+            if (cx) cx[row] = 1.0;
+            if (cy) cy[row] = 1.0;
+        } else {
+            dd Rm1, Rm;
+            int s0;
+            run_norms(&A.R, z2, row, &Rm1, &Rm, &s0);
+            dd den = dd_mul(Rm1, Rm);
+            dd zq = dd_sqrt(z2[row]);
+            int cnt = 0, head = A.R.run_head[row], p = A.R.run_pos[row];
+            for (int s = s0; s < n1 && cnt < p; s++) {
+                int r = A.R.order[s];
+                if (A.R.kind[r] == 1) continue;
+                if (A.R.run_head[r] != head) break;
+                dd f = dd_neg(dd_div(zq, den));
+                if (cx) cx[r] = dd_mul_d(f, zc[r]).hi;
+                if (cy) cy[r] = dd_mul_d(f, zr[r]).hi;
+                cnt++;
+            }
+            dd g = dd_div(Rm1, dd_mul(Rm, zq));
+            if (cx) cx[row] = dd_mul_d(g, zc[row]).hi;
+            if (cy) cy[row] = dd_mul_d(g, zr[row]).hi;
+        }
+    }
+    arrow_sol_free(&A);
+    free(za); free(z2);
+    return 0;
 }
 
 /*
@@ -760,7 +1014,7 @@ int oracle_dpr1_eig(int n, const double *d, const double *u, double rho,
     reduce(n, d, u, &R);
     int m = R.m;
     dd *c = malloc(sizeof(dd) * (m > 0 ? m : 1));
-    for (int j = 0; j < m; j++) c[j] = dd_mul(R.pole_z[j], R.pole_z[j]);
+    for (int j = 0; j < m; j++) c[j] = R.pole_c[j];
     int ncomp = (rho == 0.0) ? 0 : m;
     int ndefl = R.ndefl;
     /* with rho == 0 every pole is an eigenvalue with a unit vector */

@@ -69,6 +69,44 @@ def graded_arrow(n: int, seed: int = 1):
     return d, z, alpha
 
 
+def uniform_herm(n: int, seed: int = 8):
+    """Hermitian arrowhead (Sec. 6.1): d as uniform_arrow, |zeta| = 1 - U[0,1),
+    phase U[0, 2 pi), alpha ~ N(0,1).  Returns (d, z complex, alpha)."""
+    d, r, alpha = uniform_arrow(n, seed=seed)
+    rng = np.random.default_rng(seed + 1000)
+    z = r * np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, n - 1))
+    return d, z, alpha
+
+
+def graded_herm(n: int, seed: int = 9):
+    """Graded Hermitian arrowhead: d, |zeta| as graded_arrow, uniform phases."""
+    d, r, alpha = graded_arrow(n, seed=seed)
+    rng = np.random.default_rng(seed + 1000)
+    z = r * np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, n - 1))
+    return d, z, alpha
+
+
+def uniform_nsym(n: int, seed: int = 10):
+    """Non-symmetric arrowhead (Remark, Sec. 6.1): d as uniform_arrow; column
+    spikes zc with random signs and |zc| = 1 - U[0,1); row spikes zr = zc t,
+    t = 10^U[-2,2] (same sign).  Returns (d, zc, zr, alpha)."""
+    d, r, alpha = uniform_arrow(n, seed=seed)
+    rng = np.random.default_rng(seed + 1000)
+    zc = np.where(rng.random(n - 1) < 0.5, -1.0, 1.0) * r
+    zr = zc * 10.0 ** rng.uniform(-2.0, 2.0, n - 1)
+    return d, zc, zr, alpha
+
+
+def graded_nsym(n: int, seed: int = 11):
+    """Graded non-symmetric arrowhead: d as graded_arrow, |zc| = 10^U[-10,0],
+    zr = zc 10^U[-3,3]."""
+    d, r, alpha = graded_arrow(n, seed=seed)
+    rng = np.random.default_rng(seed + 1000)
+    zc = np.where(rng.random(n - 1) < 0.5, -1.0, 1.0) * r
+    zr = zc * 10.0 ** rng.uniform(-3.0, 3.0, n - 1)
+    return d, zc, zr, alpha
+
+
 def batch_sizes(count: int = 4096, lo: int = 32, hi: int = 4096, seed: int = 2):
     """Instance orders, log-uniform in [lo, hi]."""
     rng = np.random.default_rng(seed)
