@@ -209,7 +209,8 @@ def timed_device(fn, steps, warmup, stream, flush):
 
 
 def extras(arrowhead, W, dev, stream, flush, args):
-    """DPR1 and SVD (n = 8192), the batched set and a serving sweep."""
+    """DPR1, SVD, Hermitian and non-symmetric arrowheads (n = 8192), the batched
+    set and a serving sweep."""
     import torch
     out = {}
     prec, fin = FORMS[args.form]
@@ -243,7 +244,36 @@ def extras(arrowhead, W, dev, stream, flush, args):
     out["svd_n8192"] = {"value": n / (ms / 1e3), "unit": "singular triplets/s", "ms_per_step": ms,
                         "k_eig_ms": info["ms_eig"],
                         "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
-    del Q, U
+    # Hermitian arrowhead (Sec. 6.1), complex U
+    d, z, al = W.uniform_herm(n, seed=8)
+    dt, zt = torch.as_tensor(d, device=dev), torch.as_tensor(z, device=dev)
+    del U
+    Uc = torch.empty((n, n), dtype=torch.complex128, device=dev)
+
+    def f_herm():
+        info.update(arrowhead.herm_arrow_eig(dt, zt, al, opts=opts, info=True,
+                                             out={"lam": lam, "U": Uc}, stream=stream)["info"])
+    ms = timed_device(f_herm, 3, 1, stream, flush)
+    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval)
+    out["herm_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                         "k_eig_ms": info["ms_eig"],
+                         "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+    del Uc
+    # non-symmetric arrowhead (Remark of Sec. 6.1), right and left vectors
+    d, zc, zr, al = W.uniform_nsym(n, seed=10)
+    dt, zct, zrt = (torch.as_tensor(x, device=dev) for x in (d, zc, zr))
+    Y = torch.empty((n, n), dtype=torch.float64, device=dev)
+
+    def f_nsym():
+        info.update(arrowhead.nsym_arrow_eig(dt, zct, zrt, al, opts=opts, info=True,
+                                             out={"lam": lam, "X": Q, "Y": Y},
+                                             stream=stream)["info"])
+    ms = timed_device(f_nsym, 3, 1, stream, flush)
+    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval)
+    out["nsym_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                         "k_eig_ms": info["ms_eig"],
+                         "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+    del Q, Y
     # batched: 4096 instances, orders log-uniform in [32, 4096], one CUDA-graph plan
     inst = W.uniform_batch(4096, seed=2)
     B = arrowhead.Batch(inst, opts=arrowhead.default_opts(precision=prec, finish=fin),

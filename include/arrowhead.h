@@ -206,6 +206,66 @@ int tri_arrow_svd(int n, const double *d, const double *z, double alpha, double 
                   const ae_diag *diag, void *stream);
 
 /*
+ * herm_arrow_eig -- all eigenpairs of the Hermitian arrowhead
+ *     C = [diag(d) z; z^* alpha]                              (Sec. 6.1)
+ * of order n, z complex: z_r = zeta_r is the column above the real corner.
+ * The diagonal unitary similarity Phi = diag(zeta_r/|zeta_r|, 1) gives the
+ * real arrowhead A = Phi^* C Phi = [diag(d) |z|; |z|^T alpha] (Eq. cc), solved
+ * as arrow_eig solves it, with each |zeta_r|^2 = re^2 + im^2 in double-double
+ * (the paper asks for the moduli in doubled precision when b is); then
+ * U = Phi V, i.e. u_r = zeta_r / ((d_r - sigma) - mu) / ||x||, u_n = -1/||x||.
+ *
+ *  n       order, n >= 1                                               (arg 1)
+ *  d       device, n-1 doubles, any order                               (2)
+ *  z       device, n-1 complex numbers as 2(n-1) doubles (re, im interleaved,
+ *          the layout of cuDoubleComplex / complex128); zeta_r = 0 deflates
+ *          (d_r, e_r)                                                   (3)
+ *  alpha   the real corner                                              (4)
+ *  lambda  device, n doubles out, descending                            (5)
+ *  U, ldu  device, column-major complex n x n (column k at U + 2*ldu*k
+ *          doubles, row r at doubles 2r, 2r+1) out, or NULL; ldu >= n
+ *          complex entries.  A run of equal d gives Phi times the real
+ *          vector arrow_eig gives for the moduli                    (6, 7)
+ *  shift, mu, opts, info, diag, stream: as arrow_eig (diag refers to A)
+ *                                                               (args 8-13)
+ * Returns as arrow_eig.
+ */
+int herm_arrow_eig(int n, const double *d, const double *z, double alpha, double *lambda,
+                   double *U, int ldu, double *shift, double *mu, const ae_opts *opts,
+                   ae_info *info, const ae_diag *diag, void *stream);
+
+/*
+ * nsym_arrow_eig -- all eigenpairs of the non-symmetric arrowhead
+ *     G = [diag(d) zc; zr^T alpha]               (Remark of Sec. 6.1)
+ * of order n with zc_r zr_r > 0 (each pair of one sign), or zc_r = zr_r = 0.
+ * The diagonal similarity Psi = diag(sign(zr_r) sqrt(zc_r / zr_r), 1) gives
+ * the symmetric arrowhead A = Psi^{-1} G Psi with zeta_r = sqrt(zc_r zr_r)
+ * (zeta_r^2 = zc_r zr_r exactly in double-double); G has A's eigenvalues, right
+ * eigenvectors X = Psi V and left eigenvectors Y = Psi^{-1} V, so that
+ * x_r = zc_r t_r, y_r = zr_r t_r with t_r = 1/((d_r - sigma) - mu)/||x||,
+ * x_n = y_n = -1/||x||, and Y^T X = I.  (The printed Psi has the ratio
+ * inverted; this one makes Psi^{-1} G Psi symmetric.)
+ *
+ *  n       order, n >= 1                                               (arg 1)
+ *  d       device, n-1 doubles, any order                               (2)
+ *  zc, zr  device, n-1 doubles each: the column above the corner and the
+ *          row left of it; a pair of opposite signs, or with exactly one
+ *          zero, is reported as AE_ERR_INPUT (with info)            (3, 4)
+ *  alpha   the corner                                                   (5)
+ *  lambda  device, n doubles out, descending                            (6)
+ *  X, ldx  device, ldx*n doubles out or NULL: right eigenvectors    (7, 8)
+ *  Y, ldy  device, ldy*n doubles out or NULL (requires X): left
+ *          eigenvectors                                            (9, 10)
+ *  shift, mu, opts, info, diag, stream: as arrow_eig (diag refers to A)
+ *                                                              (args 11-16)
+ * Returns as arrow_eig.
+ */
+int nsym_arrow_eig(int n, const double *d, const double *zc, const double *zr, double alpha,
+                   double *lambda, double *X, int ldx, double *Y, int ldy, double *shift,
+                   double *mu, const ae_opts *opts, ae_info *info, const ae_diag *diag,
+                   void *stream);
+
+/*
  * Batched arrowheads: `count` independent instances of orders n_i >= 1, solved
  * together -- each stage of the arrow_eig pipeline is one persistent launch
  * over all instances (eigenpairs of every instance share one work queue and

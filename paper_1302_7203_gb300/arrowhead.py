@@ -31,6 +31,7 @@ FLAG_CAPPED, FLAG_SINGULAR, FLAG_FP32_FALLBACK = 16, 32, 64
 
 # every symbol include/arrowhead.h declares
 EXPORTED = ["ae_default_opts", "ae_status_string", "ae_last_cuda_error", "arrow_eig",
+            "herm_arrow_eig", "nsym_arrow_eig",
             "dpr1_eig", "tri_arrow_svd", "arrow_eig_batched", "ae_batch_create",
             "ae_batch_run", "ae_batch_info", "ae_batch_destroy", "ae_autotune",
             "ae_team_width", "ae_serve_create", "ae_serve_submit", "ae_serve_poll",
@@ -118,6 +119,13 @@ def lib():
         L.tri_arrow_svd.argtypes = [I, P, P, D, P, P, I, P, I, ctypes.POINTER(AeOpts),
                                     ctypes.POINTER(AeInfo), ctypes.POINTER(AeDiag), P]
         L.tri_arrow_svd.restype = I
+        L.herm_arrow_eig.argtypes = [I, P, P, D, P, P, I, P, P, ctypes.POINTER(AeOpts),
+                                     ctypes.POINTER(AeInfo), ctypes.POINTER(AeDiag), P]
+        L.herm_arrow_eig.restype = I
+        L.nsym_arrow_eig.argtypes = [I, P, P, P, D, P, P, I, P, I, P, P,
+                                     ctypes.POINTER(AeOpts), ctypes.POINTER(AeInfo),
+                                     ctypes.POINTER(AeDiag), P]
+        L.nsym_arrow_eig.restype = I
         LLP = ctypes.POINTER(ctypes.c_longlong)
         L.arrow_eig_batched.argtypes = [I, LLP, LLP, P, P, P, P, P, P, ctypes.POINTER(AeOpts),
                                         ctypes.POINTER(AeInfo), P]
@@ -322,6 +330,97 @@ def tri_arrow_svd(d, z, alpha, *, vectors=True, opts=None, info=False, diag=Fals
     if vectors:
         res["U"] = U.t()
         res["V"] = V.t()
+    if info:
+        res["info"] = inf.as_dict()
+    if diag:
+        res["diag"] = dgt
+    return res
+
+
+def herm_arrow_eig(d, z, alpha, *, vectors=True, want_shift=False, opts=None, info=False,
+                   diag=False, stream=None, out=None):
+    """Eigen-decomposition of the Hermitian arrowhead [diag(d) z; z^* alpha] (Sec. 6.1).
+
+    ``d``: float64 CUDA tensor of length n-1, ``z``: complex128 CUDA tensor of
+    length n-1 (the column above the real corner).  Returns ``lam`` (descending)
+    and ``U`` (complex, columns ``U[:, k]``) when ``vectors``; ``shift``/``mu``,
+    ``info`` and ``diag`` as arrow_eig."""
+    import torch
+    dev = d.device
+    n = int(d.numel()) + 1
+    if z.dtype != torch.complex128:
+        raise TypeError("herm_arrow_eig: z must be complex128")
+    z = z.contiguous()
+    out = dict(out or {})
+    lam = out.get("lam")
+    if lam is None:
+        lam = torch.empty(n, dtype=torch.float64, device=dev)
+    U = out.get("U") if vectors else None
+    if vectors and U is None:
+        U = torch.empty((n, n), dtype=torch.complex128, device=dev)
+    shift = torch.empty(n, dtype=torch.float64, device=dev) if want_shift else None
+    mu = torch.empty(n, dtype=torch.float64, device=dev) if want_shift else None
+    o = opts if opts is not None else default_opts()
+    inf = AeInfo() if info else None
+    dgt = _diag_arrays(n, dev) if diag else {}
+    dg = AeDiag(*(t.data_ptr() for t in dgt.values())) if diag else None
+    st = lib().herm_arrow_eig(n, _ptr(d), _ptr(z), float(alpha), _ptr(lam), _ptr(U), n,
+                              _ptr(shift), _ptr(mu), ctypes.byref(o),
+                              ctypes.byref(inf) if inf is not None else None,
+                              ctypes.byref(dg) if dg is not None else None,
+                              _stream_handle(stream))
+    _check("herm_arrow_eig", st)
+    res = {"lam": lam}
+    if vectors:
+        res["U"] = U.t()
+    if want_shift:
+        res["shift"], res["mu"] = shift, mu
+    if info:
+        res["info"] = inf.as_dict()
+    if diag:
+        res["diag"] = dgt
+    return res
+
+
+def nsym_arrow_eig(d, zc, zr, alpha, *, vectors=True, left=True, want_shift=False, opts=None,
+                   info=False, diag=False, stream=None, out=None):
+    """Eigen-decomposition of the non-symmetric arrowhead [diag(d) zc; zr^T alpha]
+    (Remark of Sec. 6.1; zc_r zr_r > 0 or both zero).
+
+    Returns ``lam`` (descending), right vectors ``X`` and (``left``) left
+    vectors ``Y`` (columns, Y^T X = I) when ``vectors``; the rest as arrow_eig."""
+    import torch
+    dev = d.device
+    n = int(d.numel()) + 1
+    out = dict(out or {})
+    lam = out.get("lam")
+    if lam is None:
+        lam = torch.empty(n, dtype=torch.float64, device=dev)
+    X = out.get("X") if vectors else None
+    Y = out.get("Y") if (vectors and left) else None
+    if vectors and X is None:
+        X = torch.empty((n, n), dtype=torch.float64, device=dev)
+    if vectors and left and Y is None:
+        Y = torch.empty((n, n), dtype=torch.float64, device=dev)
+    shift = torch.empty(n, dtype=torch.float64, device=dev) if want_shift else None
+    mu = torch.empty(n, dtype=torch.float64, device=dev) if want_shift else None
+    o = opts if opts is not None else default_opts()
+    inf = AeInfo() if info else None
+    dgt = _diag_arrays(n, dev) if diag else {}
+    dg = AeDiag(*(t.data_ptr() for t in dgt.values())) if diag else None
+    st = lib().nsym_arrow_eig(n, _ptr(d), _ptr(zc), _ptr(zr), float(alpha), _ptr(lam),
+                              _ptr(X), n, _ptr(Y), n, _ptr(shift), _ptr(mu), ctypes.byref(o),
+                              ctypes.byref(inf) if inf is not None else None,
+                              ctypes.byref(dg) if dg is not None else None,
+                              _stream_handle(stream))
+    _check("nsym_arrow_eig", st)
+    res = {"lam": lam}
+    if vectors:
+        res["X"] = X.t()
+        if left:
+            res["Y"] = Y.t()
+    if want_shift:
+        res["shift"], res["mu"] = shift, mu
     if info:
         res["info"] = inf.as_dict()
     if diag:
@@ -561,8 +660,8 @@ def exported_symbols(path=LIB_PATH):
     return [s for s in EXPORTED if hasattr(L, s)]
 
 
-__all__ = ["arrow_eig", "dpr1_eig", "tri_arrow_svd", "Batch", "Server", "autotune",
-           "arrow_eig_host",
+__all__ = ["arrow_eig", "herm_arrow_eig", "nsym_arrow_eig", "dpr1_eig", "tri_arrow_svd",
+           "Batch", "Server", "autotune", "arrow_eig_host",
            "debug_rcp", "default_opts", "lib", "AeOpts",
            "AeInfo", "AeDiag", "AeError", "exported_symbols", "EXPORTED"]
 

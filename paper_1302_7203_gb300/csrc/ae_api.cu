@@ -112,7 +112,7 @@ const char *ae_last_cuda_error(void) { return g_err; }
 // synchronising summary.
 static int solve_common(ae::Kind kind, int n, const double *d, const double *z, double alpha,
                         double rho, const ae::Outputs &out, const ae_opts *opts, ae_info *info,
-                        void *stream) {
+                        void *stream, const double *zrow = nullptr) {
     ae::RunOpts ro;
     if (ae::resolve_opts(opts, ro)) return -10;
     cudaStream_t st = (cudaStream_t)stream;
@@ -137,7 +137,7 @@ static int solve_common(ae::Kind kind, int n, const double *d, const double *z, 
     S.wbuf = (double2 *)wb;
     S.wstride = wstride;
     int status = AE_OK;
-    e = ae::launch_solve(kind, n, d, z, alpha, rho, out, ro, S, st);
+    e = ae::launch_solve(kind, n, d, z, alpha, rho, out, ro, S, st, zrow);
     if (e != cudaSuccess) status = cuda_fail(e);
     if (info && status == AE_OK) {
         int cnt[ae::C_COUNT];
@@ -236,6 +236,36 @@ int tri_arrow_svd(int n, const double *d, const double *z, double alpha, double 
     if (U && !V) return -8;
     const ae::Outputs out = make_outputs(sigma, V, ldv, U, ldu, nullptr, nullptr, diag);
     return solve_common(ae::KIND_TSVD, n, d, z, alpha, 0.0, out, opts, info, stream);
+}
+
+int herm_arrow_eig(int n, const double *d, const double *z, double alpha, double *lambda,
+                   double *U, int ldu, double *shift, double *mu, const ae_opts *opts,
+                   ae_info *info, const ae_diag *diag, void *stream) {
+    if (n < 1) return -1;
+    if (n > 1 && !d) return -2;
+    if (n > 1 && !z) return -3;
+    if (!isfinite(alpha)) return -4;
+    if (!lambda) return -5;
+    if (U && ldu < n) return -7;
+    // complex columns: ldu complex entries = 2 ldu doubles
+    const ae::Outputs out = make_outputs(lambda, U, 2 * ldu, nullptr, 0, shift, mu, diag);
+    return solve_common(ae::KIND_HERM, n, d, z, alpha, 0.0, out, opts, info, stream);
+}
+
+int nsym_arrow_eig(int n, const double *d, const double *zc, const double *zr, double alpha,
+                   double *lambda, double *X, int ldx, double *Y, int ldy, double *shift,
+                   double *mu, const ae_opts *opts, ae_info *info, const ae_diag *diag,
+                   void *stream) {
+    if (n < 1) return -1;
+    if (n > 1 && !d) return -2;
+    if (n > 1 && (!zc || !zr)) return -3;
+    if (!isfinite(alpha)) return -4;
+    if (!lambda) return -5;
+    if (X && ldx < n) return -7;
+    if (Y && !X) return -8;
+    if (Y && ldy < n) return -9;
+    const ae::Outputs out = make_outputs(lambda, X, ldx, Y, ldy, shift, mu, diag);
+    return solve_common(ae::KIND_NSYM, n, d, zc, alpha, 0.0, out, opts, info, stream, zr);
 }
 
 int arrow_eig_host(int n, const double *d_host, const double *z_host, double alpha,

@@ -33,11 +33,16 @@ namespace ae {
 // ---------------------------------------------------------------------------
 // ARROW: key d, spike z.  DPR1: key sgn d (sgn = sign of rho), spike u.
 // SVD: key d (> 0 required), spike d z.
+// HERM: spike |zeta_r| of the complex (z[2r], z[2r+1]).  NSYM: spike
+// sqrt(zc_r zr_r) of the pair (z[r], zrow[r]), which must share a sign or both
+// be zero (the Remark of Sec. 6.1).
 __global__ void k_check(Kind kind, int n1, const double *__restrict__ d,
-                        const double *__restrict__ z, double sgn, Scratch S) {
+                        const double *__restrict__ z, const double *__restrict__ zrow,
+                        double sgn, Scratch S) {
     int flags = 0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n1; r += gridDim.x * blockDim.x) {
-        const double dr = d[r], zr = z[r];
+        const double dr = d[r];
+        const double zr = kind == KIND_HERM ? z[2 * r] : z[r];
         if (!isfinite(dr) || !isfinite(zr)) flags |= CF_BAD;
         double key = dr, spk = zr;
         if (kind == KIND_DPR1) {
@@ -46,6 +51,18 @@ __global__ void k_check(Kind kind, int n1, const double *__restrict__ d,
         } else if (kind == KIND_TSVD) {
             if (!(dr > 0.0)) flags |= CF_BAD;
             spk = dr * zr;
+            S.spk[r] = spk;
+        } else if (kind == KIND_HERM) {
+            const double zi = z[2 * r + 1];
+            if (!isfinite(zi)) flags |= CF_BAD;
+            spk = hypot(zr, zi);
+            S.spk[r] = spk;
+        } else if (kind == KIND_NSYM) {
+            const double zw = zrow[r];
+            if (!isfinite(zw)) flags |= CF_BAD;
+            if ((zr == 0.0) != (zw == 0.0) || (zr != 0.0 && (zr > 0.0) != (zw > 0.0)))
+                flags |= CF_BAD;
+            spk = sqrt(fabs(zr)) * sqrt(fabs(zw));
             S.spk[r] = spk;
         }
         if (spk == 0.0) flags |= CF_ZERO;
@@ -100,9 +117,10 @@ __global__ void __launch_bounds__(1024) k_reduce(int n1, const double *__restric
 
 template <Kind K>
 __global__ void __launch_bounds__(1024) k_post(int n1, const double *__restrict__ d,
-                                               const double *__restrict__ z, double alpha,
+                                               const double *__restrict__ z,
+                                               const double *__restrict__ zrow, double alpha,
                                                double rho_abs, Scratch S) {
-    post_block<K>(n1, d, z, alpha, rho_abs, S);
+    post_block<K>(n1, d, z, zrow, alpha, rho_abs, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -160,14 +178,15 @@ __global__ void k_place(Scratch S) { place_item(S, blockIdx.x * blockDim.x + thr
 template <Kind K>
 __global__ void __launch_bounds__(256) k_vectors(int n, int n1, const double *__restrict__ key,
                                                  const double *__restrict__ spk,
-                                                 const double *__restrict__ z, double alpha,
+                                                 const double *__restrict__ z,
+                                                 const double *__restrict__ zrow, double alpha,
                                                  double sgn, Scratch S, Outputs out) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int nitems = S.cnt[C_M] + 1 + S.cnt[C_ND];
     for (int item = warp; item < nitems; item += nwarps)
-        vector_item<K>(n, n1, key, spk, z, alpha, sgn, S, out, item, lane);
+        vector_item<K>(n, n1, key, spk, z, zrow, alpha, sgn, S, out, item, lane);
 }
 
 __global__ void k_debug_rcp(int n, const double *x, double *y) {
@@ -286,12 +305,13 @@ static void launch_eig_kernels(int n, Scratch S, const SolveOpts &so, const RunO
 
 cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, double alpha,
                          double rho, const Outputs &out, const RunOpts &ro, Scratch S,
-                         cudaStream_t st) {
+                         cudaStream_t st, const double *zrow) {
     const int n1 = kind == KIND_DPR1 ? n : n - 1;
     const double sgn = (kind == KIND_DPR1 && rho < 0.0) ? -1.0 : 1.0;
     const double *key = (kind == KIND_DPR1 && sgn < 0.0) ? S.key : d;
     const bool rho0 = kind == KIND_DPR1 && rho == 0.0;   // M = D: every row deflates
-    const double *spk = (kind == KIND_TSVD || rho0) ? S.spk : z;
+    const bool own_spk = kind == KIND_TSVD || kind == KIND_HERM || kind == KIND_NSYM || rho0;
+    const double *spk = own_spk ? S.spk : z;
     cudaError_t e;
     e = cudaMemsetAsync(S.cnt, 0, sizeof(int) * C_COUNT, st);
     if (e) return e;
@@ -305,23 +325,31 @@ cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, dou
     if (ro.ev[0]) cudaEventRecord(ro.ev[0], st);
     if (n1 > 0) {
         const int g = (n1 + 255) / 256;
-        k_check<<<g, 256, 0, st>>>(kind, n1, d, z, sgn, S);
+        k_check<<<g, 256, 0, st>>>(kind, n1, d, z, zrow, sgn, S);
         k_rank<<<g, 256, 0, st>>>(n1, key, S.cnt, S.perm);
     }
     k_reduce<<<1, 1024, 0, st>>>(n1, key, spk, S.perm, S);
     SolveOpts so{ro.max_iter, ro.precision, ro.finish};
     switch (kind) {
         case KIND_ARROW:
-            k_post<KIND_ARROW><<<1, 1024, 0, st>>>(n1, d, z, alpha, 0.0, S);
+            k_post<KIND_ARROW><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
             launch_eig_kernels<KIND_ARROW>(n, S, so, ro, st);
             break;
         case KIND_DPR1:
-            k_post<KIND_DPR1><<<1, 1024, 0, st>>>(n1, d, z, alpha, fabs(rho), S);
+            k_post<KIND_DPR1><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, fabs(rho), S);
             launch_eig_kernels<KIND_DPR1>(n, S, so, ro, st);
             break;
         case KIND_TSVD:
-            k_post<KIND_TSVD><<<1, 1024, 0, st>>>(n1, d, z, alpha, 0.0, S);
+            k_post<KIND_TSVD><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
             launch_eig_kernels<KIND_TSVD>(n, S, so, ro, st);
+            break;
+        case KIND_HERM:
+            k_post<KIND_HERM><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
+            launch_eig_kernels<KIND_ARROW>(n, S, so, ro, st);
+            break;
+        case KIND_NSYM:
+            k_post<KIND_NSYM><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
+            launch_eig_kernels<KIND_ARROW>(n, S, so, ro, st);
             break;
     }
     k_place<<<(n + 255) / 256, 256, 0, st>>>(S);
@@ -329,13 +357,24 @@ cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, dou
     vgrid = vgrid < sms * 16 ? vgrid : sms * 16;
     switch (kind) {
         case KIND_ARROW:
-            k_vectors<KIND_ARROW><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, alpha, sgn, S, out);
+            k_vectors<KIND_ARROW><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, zrow, alpha, sgn, S,
+                                                        out);
             break;
         case KIND_DPR1:
-            k_vectors<KIND_DPR1><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, alpha, sgn, S, out);
+            k_vectors<KIND_DPR1><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, zrow, alpha, sgn, S,
+                                                       out);
             break;
         case KIND_TSVD:
-            k_vectors<KIND_TSVD><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, alpha, sgn, S, out);
+            k_vectors<KIND_TSVD><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, zrow, alpha, sgn, S,
+                                                       out);
+            break;
+        case KIND_HERM:
+            k_vectors<KIND_HERM><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, zrow, alpha, sgn, S,
+                                                       out);
+            break;
+        case KIND_NSYM:
+            k_vectors<KIND_NSYM><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, zrow, alpha, sgn, S,
+                                                       out);
             break;
     }
     if (ro.ev[4]) cudaEventRecord(ro.ev[4], st);

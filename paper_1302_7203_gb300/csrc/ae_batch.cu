@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(1024) k_batch_prep(const BatchInst *__restrict
     __syncthreads();
     reduce_block(n1, B.d, B.z, S.perm, S);
     __syncthreads();
-    post_block<KIND_ARROW>(n1, B.d, B.z, *B.alpha, 0.0, S);
+    post_block<KIND_ARROW>(n1, B.d, B.z, nullptr, *B.alpha, 0.0, S);
 }
 
 // buf: this warp's 4 slices of stored (delta_j, c_j) pairs, `stride` apart
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_batch_vectors(const BatchInst *__restri
         if (t >= total) break;
         const int i = find_inst(eoff, count, t);
         const BatchInst &B = I[i];
-        vector_item<KIND_ARROW>(B.n, B.n1, B.d, B.z, B.z, *B.alpha, 1.0, B.S, B.out,
+        vector_item<KIND_ARROW>(B.n, B.n1, B.d, B.z, B.z, nullptr, *B.alpha, 1.0, B.S, B.out,
                                 (int)(t - eoff[i]), lane);
         __syncwarp();
     }

@@ -30,7 +30,10 @@ enum { C64_ITERS = 0, C64_MAXKB = 1, C64_MAXKNU = 2, C64_ITERS_FIX = 3, C64_COUN
 enum { CF_UNSORTED = 1, CF_ZERO = 2, CF_BAD = 4, CF_ZEROPOLE = 8 };
 
 // problem kinds sharing the pipeline
-enum Kind { KIND_ARROW = 0, KIND_DPR1 = 1, KIND_TSVD = 2 };
+// (HERM and NSYM are solved as the real arrowhead with spikes |zeta_r|, resp.
+// sqrt(zc_r zr_r), and exact double-double squares; they differ only in the
+// input check, the squares and the vector epilogue)
+enum Kind { KIND_ARROW = 0, KIND_DPR1 = 1, KIND_TSVD = 2, KIND_HERM = 3, KIND_NSYM = 4 };
 
 // slots of the per-solve double parameters
 enum {
@@ -95,10 +98,13 @@ size_t arrow_scratch_bytes(int n);
 int eig_grid_warps(int n);
 Scratch carve_scratch(void *base, int n);
 // Issue a whole solve on `st`.  ARROW: d, z have n-1 entries; DPR1: d, u (in z)
-// have n entries and rho is used; SVD: d, z have n-1 entries.
+// have n entries and rho is used; SVD: d, z have n-1 entries; HERM: z holds n-1
+// complex spikes (re, im interleaved), out.V is complex (ldv in doubles); NSYM:
+// z the column spikes, zrow the row spikes, out.V / out.U the right / left
+// vectors.
 cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, double alpha,
                          double rho, const Outputs &out, const RunOpts &ro, Scratch S,
-                         cudaStream_t st);
+                         cudaStream_t st, const double *zrow = nullptr);
 inline cudaError_t launch_arrow(int n, const double *d, const double *z, double alpha,
                                 const Outputs &out, const RunOpts &ro, Scratch S,
                                 cudaStream_t st) {

@@ -148,7 +148,8 @@ __device__ __forceinline__ dd block_sum_dd(dd v, double *sh) {
 // (single CTA of 1024 threads).
 template <Kind K>
 __device__ void post_block(int n1, const double *__restrict__ d, const double *__restrict__ z,
-                           double alpha, double rho_abs, const Scratch &S) {
+                           const double *__restrict__ zrow, double alpha, double rho_abs,
+                           const Scratch &S) {
     __shared__ double sh[64];
     int m = S.cnt[C_M];
     dd al = {alpha, 0.0};
@@ -199,6 +200,21 @@ __device__ void post_block(int n1, const double *__restrict__ d, const double *_
         }
         const int nd = S.cnt[C_ND];
         for (int t = threadIdx.x; t < nd; t += blockDim.x) S.dval[t] = S.dval[t] * S.dval[t];
+    } else if (K == KIND_HERM || K == KIND_NSYM) {
+        // a single-row pole's spike^2 exactly in double-double: |zeta|^2 =
+        // re^2 + im^2 (Sec. 6.1), resp. zc zr (its Remark), as the paper asks
+        // for the moduli in doubled precision when b is computed so
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const int r = S.prow[j];
+            if (S.pz[j] != S.spk[r]) continue;      // another row was folded in
+            const dd z2 = K == KIND_HERM
+                              ? dd_add(two_prod(z[2 * r], z[2 * r]),
+                                       two_prod(z[2 * r + 1], z[2 * r + 1]))
+                              : two_prod(z[r], zrow[r]);
+            S.pz2[j] = z2.hi;
+            S.pz2lo[j] = z2.lo;
+            S.pz[j] = dd_sqrt(z2).hi;
+        }
     }
     if (threadIdx.x == 0) {
         S.prm[P_ALPHA_HI] = al.hi;
@@ -241,6 +257,10 @@ struct PolesOf<KIND_ARROW> {
 };
 template <>
 struct PolesOf<KIND_DPR1> : PolesOf<KIND_ARROW> {};
+template <>
+struct PolesOf<KIND_HERM> : PolesOf<KIND_ARROW> {};
+template <>
+struct PolesOf<KIND_NSYM> : PolesOf<KIND_ARROW> {};
 template <>
 struct PolesOf<KIND_TSVD> {
     using type = TsvdPoles;
@@ -440,19 +460,28 @@ __device__ __forceinline__ void run_column(const Scratch &S, const double *spk, 
 // Output of item `item` (a computed eigenpair, or a deflated row) by one warp:
 // value, optional shift/mu/diagnostics, and its column(s).  `key`/`spk` are the
 // transformed inputs the reduction saw; z is the caller's spike array (SVD:
-// for the left vectors).
+// for the left vectors; HERM: the complex spikes; NSYM: the column spikes,
+// zrow the row spikes).
+// HERM writes U = Phi V (Sec. 6.1) as complex columns, row r at doubles 2r,
+// 2r+1: u_r = zeta_r t_r / ||x|| with t_r = 1/((d_r - sigma) - mu), since
+// Phi_r |zeta_r| = zeta_r.  NSYM writes the right vectors X = Psi V into V and
+// the left ones Y = Psi^{-1} V into U: x_r = zc_r t_r / ||x||, y_r = zr_r t_r
+// / ||x||, since Psi_r sqrt(zc_r zr_r) = zc_r; then y^T x = 1.
 template <Kind K>
 __device__ void vector_item(int n, int n1, const double *__restrict__ key,
                             const double *__restrict__ spk, const double *__restrict__ z,
-                            double alpha, double sgn, const Scratch &S, const Outputs &out,
-                            int item, int lane) {
+                            const double *__restrict__ zrow, double alpha, double sgn,
+                            const Scratch &S, const Outputs &out, int item, int lane) {
+    constexpr bool CPLX = K == KIND_HERM;
+    constexpr bool TWO = K == KIND_NSYM;
+    constexpr int RS = CPLX ? 2 : 1;           // doubles per row
     const int m = S.cnt[C_M];
     const int ncomp = m + 1;
     const bool last_row = K != KIND_DPR1;     // arrowhead rows have the x_n = -1 entry
     int pos = S.pos[item];
     if (K == KIND_DPR1 && sgn < 0.0) pos = n - 1 - pos;   // -M's order reversed
     double *col = out.V ? out.V + (size_t)pos * out.ldv : nullptr;
-    double *ucol = (K == KIND_TSVD && out.U) ? out.U + (size_t)pos * out.ldu : nullptr;
+    double *ucol = ((K == KIND_TSVD || TWO) && out.U) ? out.U + (size_t)pos * out.ldu : nullptr;
     if (item < ncomp) {
         const int k = item;
         const double sig = S.es_sigma[k], mu = S.es_mu[k];
@@ -484,10 +513,9 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
             if (out.dg_flags) out.dg_flags[pos] = S.es_flags[k];
         }
         if (!col) return;
-        // component of row r: spike_r / (shifted difference of row r - mu)
-        auto comp = [&](int r) {
-            const double sr = spk[r];
-            if (sr == 0.0) return 0.0;
+        // 1/(shifted difference of row r - mu); 0 for a zero spike
+        auto recip = [&](int r) {
+            if (spk[r] == 0.0) return 0.0;
             double del;
             if (K == KIND_TSVD) {
                 const double dr = key[r];
@@ -500,17 +528,26 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
             } else {
                 del = key[r] - sig;
             }
-            return sr * rcp(del - mu);
+            return rcp(del - mu);
         };
-        // Pass 1 stores x in the column and sums x^2 in sorted order (so the
-        // norm does not depend on the order of the input rows); pass 2
-        // scales in place.
+        // component of row r of x = [(D - lambda I)^{-1} spikes; -1]
+        auto comp = [&](int r) { return spk[r] * recip(r); };
+        // Pass 1 stores x (HERM, NSYM: the reciprocal t) in the column and sums
+        // x^2 in sorted order (so the norm does not depend on the order of the
+        // input rows); pass 2 scales in place.
         double s = 0.0;
         for (int q = lane; q < n1; q += 32) {
             const int r = S.perm[q];
-            const double x = comp(r);
-            col[r] = x;
-            s = fma(x, x, s);
+            if (CPLX || TWO) {
+                const double t = recip(r);
+                col[RS * r] = t;
+                const double x = spk[r] * t;
+                s = fma(x, x, s);
+            } else {
+                const double x = comp(r);
+                col[r] = x;
+                s = fma(x, x, s);
+            }
         }
         s = warp_sum(s) + (last_row ? 1.0 : 0.0);
         double inv, scale = 1.0;
@@ -536,15 +573,26 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
         const double vs = (K == KIND_DPR1 && sgn < 0.0) ? -1.0 : 1.0;
         __syncwarp();
         for (int r = lane; r < n1; r += 32) {
-            const double x = stored ? col[r] : comp(r) * scale;
-            const double v = vs * x * inv;
-            col[r] = v;
-            if (ucol) ucol[r] = sv * v / key[r];      // u_j = s v_j / d_j
+            if (CPLX) {
+                const double t = (stored ? col[2 * r] : recip(r) * scale) * inv;
+                col[2 * r] = z[2 * r] * t;
+                col[2 * r + 1] = z[2 * r + 1] * t;
+            } else if (TWO) {
+                const double t = (stored ? col[r] : recip(r) * scale) * inv;
+                col[r] = z[r] * t;
+                if (ucol) ucol[r] = zrow[r] * t;
+            } else {
+                const double x = stored ? col[r] : comp(r) * scale;
+                const double v = vs * x * inv;
+                col[r] = v;
+                if (ucol) ucol[r] = sv * v / key[r];      // u_j = s v_j / d_j
+            }
         }
         if (last_row && lane == 0) {
             const double vn = -scale * inv;
-            col[n1] = vn;
-            if (ucol) ucol[n1] = alpha * vn / sv;    // u_n = alpha v_n / s
+            col[RS * n1] = vn;
+            if (CPLX) col[RS * n1 + 1] = 0.0;
+            if (ucol) ucol[n1] = K == KIND_TSVD ? alpha * vn / sv : vn;   // SVD: u_n = alpha v_n / s
         }
     } else {
         const int u = item - ncomp;
@@ -562,14 +610,49 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
             if (out.dg_flags) out.dg_flags[pos] = AE_FLAG_DEFLATED;
         }
         if (!col) return;
-        for (int r = lane; r < n; r += 32) col[r] = 0.0;
+        for (int r = lane; r < RS * n; r += 32) col[r] = 0.0;
+        if (TWO && ucol)
+            for (int r = lane; r < n; r += 32) ucol[r] = 0.0;
         __syncwarp();
         if (S.kind[row] == 1) {
-            if (lane == 0) col[row] = 1.0;
+            if (lane == 0) {
+                col[RS * row] = 1.0;
+                if (TWO && ucol) ucol[row] = 1.0;
+            }
+        } else if (CPLX || TWO) {
+            // Phi (resp. Psi, Psi^{-1}) times the real Helmert-type vector of
+            // the moduli: rows l before `row` in its run get -|zeta_q| s_l /
+            // (R_{m-1} R_m), the row itself (s_q / |zeta_q|) R_{m-1} / R_m, with
+            // s the caller's spike (zeta, zc or zr)
+            const double Rm1 = S.run_R[2 * row], Rm = S.run_R[2 * row + 1];
+            const double zq = spk[row];
+            const double f = -zq / (Rm1 * Rm);
+            const int s0 = S.run_s0[row], s1 = S.spos[row];
+            for (int q = s0 + lane; q < s1; q += 32) {
+                const int rq = S.perm[q];
+                if (spk[rq] == 0.0) continue;
+                if (CPLX) {
+                    col[2 * rq] = f * z[2 * rq];
+                    col[2 * rq + 1] = f * z[2 * rq + 1];
+                } else {
+                    col[rq] = f * z[rq];
+                    if (ucol) ucol[rq] = f * zrow[rq];
+                }
+            }
+            if (lane == 0) {
+                const double g = Rm1 / (Rm * zq);
+                if (CPLX) {
+                    col[2 * row] = g * z[2 * row];
+                    col[2 * row + 1] = g * z[2 * row + 1];
+                } else {
+                    col[row] = g * z[row];
+                    if (ucol) ucol[row] = g * zrow[row];
+                }
+            }
         } else {
             run_column(S, spk, row, lane, col, 1.0);
         }
-        if (ucol) {
+        if (K == KIND_TSVD && ucol) {
             // B v = d_r v for a deflated right vector (its last entry is 0)
             __syncwarp();
             for (int r = lane; r < n; r += 32) ucol[r] = col[r];
