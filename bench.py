@@ -19,7 +19,10 @@ roofline   the eigenvalue kernel (k_eig): algorithmic FP64 flops per launch
            FP64 ALU peak 152 SMs x 4 flop/clk x 2070 MHz.  Also reported: the
            all-FP64 bisection's algorithmic work over the headline form's k_eig
            time (fp64_bisection_equivalent_tflops).
-forms      fp64_newton (default headline): FP64 throughout, the bracketed
+forms      fp64_newton_gated: fp64_newton with Algorithm 5's precision gates
+           (b in standard precision unless the spike ratio and K_b ask
+           for double-double).
+           fp64_newton (default headline): FP64 throughout, the bracketed
            Newton finish (same Pick function, bracket and stop test as
            Algorithm 3); fp64: all-FP64 bisection as in Algorithm 3; fp32:
            FP32 opening bracket then FP64 bisection; fp32_newton.  All four are
@@ -72,8 +75,14 @@ def csrc_sha256():
     return h.hexdigest()
 
 
-# solver forms: (ae_opts.precision, ae_opts.finish)
-FORMS = {"fp32": (1, 0), "fp64": (0, 0), "fp32_newton": (1, 1), "fp64_newton": (0, 1)}
+# solver forms: (ae_opts.precision, ae_opts.finish, ae_opts.bgate)
+FORMS = {"fp32": (1, 0, 0), "fp64": (0, 0, 0), "fp32_newton": (1, 1, 0),
+         "fp64_newton": (0, 1, 0), "fp64_newton_gated": (0, 1, 1)}
+
+
+def form_opts(arrowhead, form, **kw):
+    prec, fin, gate = FORMS[form]
+    return arrowhead.default_opts(precision=prec, finish=fin, bgate=gate, **kw)
 
 
 def parse():
@@ -213,9 +222,8 @@ def extras(arrowhead, W, dev, stream, flush, args):
     set and a serving sweep."""
     import torch
     out = {}
-    prec, fin = FORMS[args.form]
-    per_eval = 6.0 if fin == 1 else 3.0
-    opts = arrowhead.default_opts(precision=prec, finish=fin, profile=1)
+    per_eval = 6.0 if FORMS[args.form][1] == 1 else 3.0
+    opts = form_opts(arrowhead, args.form, profile=1)
     n = 8192
     d, u, rho = W.uniform_dpr1(n, seed=3)
     dt, ut = torch.as_tensor(d, device=dev), torch.as_tensor(u, device=dev)
@@ -276,8 +284,7 @@ def extras(arrowhead, W, dev, stream, flush, args):
     del Q, Y
     # batched: 4096 instances, orders log-uniform in [32, 4096], one CUDA-graph plan
     inst = W.uniform_batch(4096, seed=2)
-    B = arrowhead.Batch(inst, opts=arrowhead.default_opts(precision=prec, finish=fin),
-                        stream=stream)
+    B = arrowhead.Batch(inst, opts=form_opts(arrowhead, args.form), stream=stream)
     ms = timed_device(lambda: B.run(), 2, 1, stream, flush)
     binfo = B.run(info=True)
     tot_n = int(B.n_off[-1])
@@ -292,7 +299,7 @@ def extras(arrowhead, W, dev, stream, flush, args):
     torch.cuda.empty_cache()
     # serving: Poisson arrivals of mixed kinds, orders log-uniform in [64, 16384]
     out["serving"] = serve_sweep(arrowhead, W, dev, args.serve_requests,
-                                 arrowhead.default_opts(precision=prec, finish=fin))
+                                 form_opts(arrowhead, args.form))
     return out
 
 
@@ -404,8 +411,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def timed(form):
-        prec, fin = FORMS[form]
-        opts = arrowhead.default_opts(precision=prec, finish=fin, profile=1)
+        opts = form_opts(arrowhead, form, profile=1)
 
         def step():
             return arrowhead.arrow_eig(dt, zt, alpha, opts=opts, info=True,
@@ -474,7 +480,7 @@ def main():
         zh = torch.as_tensor(z).pin_memory()
         lh = torch.empty(n, dtype=torch.float64).pin_memory()
         Vh = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        eopts = arrowhead.default_opts(precision=FORMS[primary][0], finish=FORMS[primary][1])
+        eopts = form_opts(arrowhead, primary)
         arrowhead.arrow_eig_host(dh, zh, alpha, opts=eopts, out={"lam": lh, "V": Vh},
                                  stream=stream)
         t0 = time.perf_counter()
@@ -509,7 +515,8 @@ def main():
                 "value": world * n * args.steps / (tot / 1e3), "ms_per_step": tot / args.steps,
                 "ms_eig": float(np.mean([x["ms_eig"] for x in inf])),
                 "fp64_steps_per_eigenpair": inf[-1]["total_iter"] / n,
-                "fp32_fallbacks": inf[-1]["n_fp32_fallback"]}
+                "fp32_fallbacks": inf[-1]["n_fp32_fallback"],
+                "b_double_double": inf[-1]["n_ddb"]}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,

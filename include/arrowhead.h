@@ -63,6 +63,7 @@ extern "C" {
 #define AE_FLAG_CAPPED 16     /* bisection stopped at max_iter */
 #define AE_FLAG_SINGULAR 32   /* remedy found a zero denominator: lambda = sigma */
 #define AE_FLAG_FP32_FALLBACK 64 /* FP32 bracket failed its FP64 check */
+#define AE_FLAG_DDB 128       /* with opts->bgate: b recomputed in double-double */
 
 typedef struct ae_opts {
     int precision;     /* AE_FP64 (default) or AE_FP32_BRACKET */
@@ -78,6 +79,14 @@ typedef struct ae_opts {
                           to bisection when a step leaves the bracket or after 12
                           steps.  Not in the paper: a faster finish to the same
                           tolerance.  DPR1-shift remedies always bisect. */
+    int bgate;         /* 0 (default): the element b of Eq. (b_ob) always in
+                          double-double.  1: Algorithm 5's gates -- b in
+                          standard precision unless the spike ratio
+                          sum_{j != i} |zeta_j| / |zeta_i| exceeds n (C2 (ii)
+                          fails) and K_b of Eq. (K2) exceeds kb_max (C2 (i)
+                          fails); then in double-double (flag AE_FLAG_DDB) */
+    double kb_max;     /* K_b above which the gate asks for double-double;
+                          default 10 */
 } ae_opts;
 
 /* Summary counters, filled on the host when passed (forces a stream sync). */
@@ -98,6 +107,8 @@ typedef struct ae_info {
     float ms_eig;         /* eigenvalue kernel (shift, b, bisection) */
     float ms_fix;         /* remedy decisions and recomputations */
     float ms_vectors;     /* placement and eigenvector columns */
+    int n_ddb;            /* with opts->bgate: eigenpairs whose b was recomputed in
+                             double-double */
 } ae_info;
 
 /* Optional per-eigenpair diagnostics (device arrays of length n, any may be

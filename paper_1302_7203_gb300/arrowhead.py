@@ -27,7 +27,7 @@ AE_FP32_BRACKET = 1
 AE_FINISH_BISECT = 0
 AE_FINISH_NEWTON = 1
 FLAG_DEFLATED, FLAG_NEARZERO, FLAG_OTHERPOLE, FLAG_DPR1SHIFT = 1, 2, 4, 8
-FLAG_CAPPED, FLAG_SINGULAR, FLAG_FP32_FALLBACK = 16, 32, 64
+FLAG_CAPPED, FLAG_SINGULAR, FLAG_FP32_FALLBACK, FLAG_DDB = 16, 32, 64, 128
 
 # every symbol include/arrowhead.h declares
 EXPORTED = ["ae_default_opts", "ae_status_string", "ae_last_cuda_error", "arrow_eig",
@@ -46,7 +46,8 @@ AE_ERR_TOO_LARGE = 1004
 class AeOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("knu_max", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("fixup", ctypes.c_int),
-                ("profile", ctypes.c_int), ("finish", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("finish", ctypes.c_int),
+                ("bgate", ctypes.c_int), ("kb_max", ctypes.c_double)]
 
 
 class AeInfo(ctypes.Structure):
@@ -58,7 +59,7 @@ class AeInfo(ctypes.Structure):
                 ("max_Kb", ctypes.c_double),
                 ("max_Knu", ctypes.c_double), ("ms_reduce", ctypes.c_float),
                 ("ms_eig", ctypes.c_float), ("ms_fix", ctypes.c_float),
-                ("ms_vectors", ctypes.c_float)]
+                ("ms_vectors", ctypes.c_float), ("n_ddb", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -69,8 +69,11 @@ int resolve_opts(const ae_opts *o, RunOpts &ro) {
     if (!o) o = &def;
     if (o->precision != AE_FP64 && o->precision != AE_FP32_BRACKET) return 1;
     if (o->finish != AE_FINISH_BISECT && o->finish != AE_FINISH_NEWTON) return 1;
+    if (o->bgate != 0 && o->bgate != 1) return 1;
     ro.precision = o->precision;
     ro.finish = o->finish;
+    ro.bgate = o->bgate;
+    ro.kb_max = o->kb_max > 0.0 ? o->kb_max : def.kb_max;
     ro.knu_max = o->knu_max > 0.0 ? o->knu_max : def.knu_max;
     ro.max_iter = o->max_iter > 0 ? o->max_iter : def.max_iter;
     ro.fixup = o->fixup ? 1 : 0;
@@ -89,6 +92,8 @@ void ae_default_opts(ae_opts *opts) {
     opts->fixup = 1;
     opts->profile = 0;
     opts->finish = AE_FINISH_BISECT;
+    opts->bgate = 0;
+    opts->kb_max = 10.0;
 }
 
 const char *ae_status_string(int status) {
@@ -162,6 +167,7 @@ static int solve_common(ae::Kind kind, int n, const double *d, const double *z, 
             info->fix_iter = (long long)c64[ae::C64_ITERS_FIX];
             info->max_Kb = bits_to_double(c64[ae::C64_MAXKB]);
             info->max_Knu = bits_to_double(c64[ae::C64_MAXKNU]);
+            info->n_ddb = cnt[ae::C_DDB];
             if (prof.on) {
                 cudaEventElapsedTime(&info->ms_reduce, prof.ev[0], prof.ev[1]);
                 cudaEventElapsedTime(&info->ms_eig, prof.ev[1], prof.ev[2]);

@@ -329,7 +329,7 @@ cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, dou
         k_rank<<<g, 256, 0, st>>>(n1, key, S.cnt, S.perm);
     }
     k_reduce<<<1, 1024, 0, st>>>(n1, key, spk, S.perm, S);
-    SolveOpts so{ro.max_iter, ro.precision, ro.finish};
+    SolveOpts so{ro.max_iter, ro.precision, ro.finish, ro.bgate, ro.kb_max};
     switch (kind) {
         case KIND_ARROW:
             k_post<KIND_ARROW><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);

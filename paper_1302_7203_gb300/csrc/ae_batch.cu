@@ -414,7 +414,7 @@ static cudaError_t build_plan(Plan *P, int count, const long long *n_off, const 
     P->count = count;
     P->status = status_all;
     P->ro = ro;
-    P->so = SolveOpts{ro.max_iter, ro.precision, ro.finish};
+    P->so = SolveOpts{ro.max_iter, ro.precision, ro.finish, ro.bgate, ro.kb_max};
     std::vector<size_t> soff(count + 1, 0);
     for (int i = 0; i < count; ++i) {
         const int n = (int)(n_off[i + 1] - n_off[i]);
@@ -512,6 +512,7 @@ static cudaError_t plan_info(const Plan &P, ae_info *info, cudaStream_t st) {
         info->n_dpr1shift += c[C_DPR1];
         info->n_capped += c[C_CAPPED];
         info->n_fp32_fallback += c[C_FP32FB];
+        info->n_ddb += c[C_DDB];
         if (c[C_MAXIT] > info->max_iter_used) info->max_iter_used = c[C_MAXIT];
         info->total_iter += (long long)u[C64_ITERS];
         info->fix_iter += (long long)u[C64_ITERS_FIX];

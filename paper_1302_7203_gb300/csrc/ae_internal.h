@@ -22,6 +22,7 @@ enum {
     C_CAPPED = 9,
     C_MAXIT = 10,
     C_FP32FB = 11,
+    C_DDB = 12,       // b recomputed in double-double under the Algorithm 5 gate
     C_COUNT = 16
 };
 enum { C64_ITERS = 0, C64_MAXKB = 1, C64_MAXKNU = 2, C64_ITERS_FIX = 3, C64_COUNT = 4 };
@@ -42,6 +43,7 @@ enum {
     P_PLAST = 2,      // DPR1: the last reduced pole (not an arrowhead pole)
     P_DS = 3,         // FP32 copies: pole scale
     P_ZS = 4,         // FP32 copies: spike^2 scale
+    P_ZSUM = 5,       // sum of the reduced |zeta_j| (Algorithm 5's spike ratio)
     P_COUNT = 8
 };
 
@@ -86,6 +88,8 @@ struct RunOpts {
     int max_iter;
     int fixup;
     int finish;
+    int bgate;
+    double kb_max;
     cudaEvent_t ev[5];   // phase boundaries when profiling (else null)
 };
 

@@ -220,6 +220,12 @@ __device__ void post_block(int n1, const double *__restrict__ d, const double *_
         S.prm[P_ALPHA_HI] = al.hi;
         S.prm[P_ALPHA_LO] = al.lo;
     }
+    // Algorithm 5's spike ratio needs sum_j |zeta_j| over the reduced poles
+    __syncthreads();
+    double zsum = 0.0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) zsum += S.pz[j];
+    zsum = block_sum_dd(dd{zsum, 0.0}, sh).hi;
+    if (threadIdx.x == 0) S.prm[P_ZSUM] = zsum;
     // FP32 copies: keys and spike^2 scaled by powers of two so that the
     // largest of each is O(1)
     double mxd = 0.0, mxz = 0.0;
@@ -252,7 +258,7 @@ struct PolesOf<KIND_ARROW> {
     __device__ static ArrowPoles make(const Scratch &S, int m) {
         return {m,      S.pd,  S.pz,  S.pz2,          S.pz2lo,        S.prm[P_ALPHA_HI],
                 S.prm[P_ALPHA_LO], S.pdh, S.pdl,      S.pz2f,         S.prm[P_DS],
-                S.prm[P_ZS]};
+                S.prm[P_ZS],       S.prm[P_ZSUM]};
     }
 };
 template <>
@@ -267,7 +273,7 @@ struct PolesOf<KIND_TSVD> {
     __device__ static TsvdPoles make(const Scratch &S, int m) {
         return {m,     S.pd,     S.pv,              S.pz,  S.pz2, S.pz2lo,
                 S.prm[P_ALPHA_HI], S.prm[P_ALPHA_LO], S.pdh, S.pdl, S.pz2f,
-                S.prm[P_DS],       S.prm[P_ZS]};
+                S.prm[P_DS],       S.prm[P_ZS],       S.prm[P_ZSUM]};
     }
 };
 
@@ -288,6 +294,7 @@ __device__ __forceinline__ void record_stats(const Scratch &S, const EigResult &
     atomicMax(S.cnt + C_MAXIT, r.iters);
     if (r.flags & AE_FLAG_CAPPED) atomicAdd(S.cnt + C_CAPPED, 1);
     if (r.flags & AE_FLAG_FP32_FALLBACK) atomicAdd(S.cnt + C_FP32FB, 1);
+    if (r.flags & AE_FLAG_DDB) atomicAdd(S.cnt + C_DDB, 1);
     if (isfinite(r.Kb)) atomic_max_nonneg(S.cnt64 + C64_MAXKB, r.Kb);
 }
 

@@ -32,6 +32,8 @@ struct SolveOpts {
     int max_iter;
     int precision;
     int finish;     // 0: bisection (Algorithm 3); 1: bracketed Newton
+    int bgate;      // 0: b always double-double; 1: Algorithm 5's gates
+    double kb_max;  // the gate's "K_b >> 1" threshold
 };
 
 struct EigResult {
@@ -131,6 +133,7 @@ struct ArrowPoles {
     const float *__restrict__ pdl;
     const float *__restrict__ pz2f;
     double ds, zs;
+    double zsum;                     // sum of zeta_j (Algorithm 5's spike ratio)
 
     __device__ __forceinline__ double pole(int j) const { return __ldg(pd + j); }
     // p_j - shift in double; `i` is the shift's pole index (-1: not a pole)
@@ -177,6 +180,7 @@ struct TsvdPoles {
     const float *__restrict__ pdl;
     const float *__restrict__ pz2f;
     double ds, zs;
+    double zsum;                     // sum of |d_j z_j|
 
     __device__ __forceinline__ double pole(int j) const { return __ldg(pv + j); }
     __device__ __forceinline__ double shifted(int j, double shift, int i) const {
@@ -398,7 +402,10 @@ struct PassA {
 // pole shift (skip >= 0) and poles sorted decreasingly, delta_j > 0 exactly
 // for j < skip, so the two sums come from two branch-free index ranges.  The
 // stored pair is (delta_j, q1).
-template <bool GERSH = true, class P, class Team>
+// DD = false (Algorithm 5's standard precision): plain double differences,
+// quotients and sums, 7 instead of ~21 FP64 instructions a term; the stored
+// pairs are the same values.
+template <bool GERSH = true, bool DD = true, class P, class Team>
 __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift, int skip,
                                         double wscale, double2 *buf = nullptr) {
     dd s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
@@ -406,12 +413,20 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
     double pmax = -INFINITY, pmin = INFINITY, up = -INFINITY, lo = INFINITY, wsum = 0.0,
            usq = 0.0;
     auto term = [&](int j, double &dhi) -> dd {
-        const dd del = R.shifted_dd(j, shift, skip);
-        const dd z2 = R.z2_dd(j);
-        const double p = rcp(del.hi);
-        const double q1 = z2.hi * p;
-        const double res = fma(-q1, del.lo, fma(-q1, del.hi, z2.hi) + z2.lo);
-        const double q2 = res * p;
+        dd del;
+        double q1, q2 = 0.0, p;
+        if (DD) {
+            del = R.shifted_dd(j, shift, skip);
+            const dd z2 = R.z2_dd(j);
+            p = rcp(del.hi);
+            q1 = z2.hi * p;
+            const double res = fma(-q1, del.lo, fma(-q1, del.hi, z2.hi) + z2.lo);
+            q2 = res * p;
+        } else {
+            del = dd{R.shifted(j, shift, skip), 0.0};
+            p = rcp(del.hi);
+            q1 = R.z2(j) * p;
+        }
         if (buf) buf[j] = make_double2(del.hi, q1);   // (delta_j, zeta_j^2 / delta_j)
         if (GERSH) {
             const double aw = R.zabs(j) * fabs(p);
@@ -426,6 +441,10 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
         return dd{q1, q2};
     };
     auto add = [](dd &acc, int &cnt, dd t) {
+        if (!DD) {
+            acc.hi += t.hi;
+            return;
+        }
         csum_add(acc, t);
         if (++cnt == 16) {
             acc = fast_two_sum(acc.hi, acc.lo);
@@ -678,8 +697,26 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
     const double wz = 1.0 / zi;         // w_zeta
     const double c = wz * wz;           // 1/zeta_i^2
     const bool newton = o.finish == 1;
-    const PassA A = newton ? pass_a<false>(R, T, sigma, i, wz, buf)
-                           : pass_a<true>(R, T, sigma, i, wz, buf);
+    PassA A;
+    if (o.bgate) {
+        // Algorithm 5: b in standard precision unless both C2 (i) and C2 (ii)
+        // fail -- the spike ratio sum_{j != i} |zeta_j| / |zeta_i| exceeds the
+        // order n and K_b of Eq. (K2) from the standard sums exceeds kb_max --
+        // then P and Q again in double-double (Theorem 6)
+        A = newton ? pass_a<false, false>(R, T, sigma, i, wz, buf)
+                   : pass_a<true, false>(R, T, sigma, i, wz, buf);
+        const double ratio = (R.zsum - zi) / zi;
+        const double Kb0 = (A.P.hi + A.Q.hi) / fabs(A.P.hi - A.Q.hi);
+        if (ratio > (double)(R.m + 1) && !(Kb0 <= o.kb_max)) {
+            const PassA D = pass_a<false, true>(R, T, sigma, i, wz);
+            A.P = D.P;
+            A.Q = D.Q;
+            res.flags |= 128;                  // AE_FLAG_DDB
+        }
+    } else {
+        A = newton ? pass_a<false>(R, T, sigma, i, wz, buf)
+                   : pass_a<true>(R, T, sigma, i, wz, buf);
+    }
     // b = (P - Q) / zeta_i^2 in double-double (Theorem 6), rounded once
     const dd num = dd_add(A.P, dd_neg(A.Q));
     const double b = dd_div(num, two_prod(zi, zi)).hi;
