@@ -4,7 +4,7 @@
 Workload: the graded arrowhead of order n = 16384 (|d| = 10^U[-15,0] with random
 signs, z = 10^U[-10,0], alpha = 1e3), all n eigenpairs with the full n x n
 eigenvector matrix in FP64.  One step = one complete arrow_eig call (reduction,
-shift-and-invert bisection for every eigenvalue, remedies, vectors).
+shift-and-invert solve for every eigenvalue, remedies, vectors).
 
 value      eigenpairs/s of the whole job, inputs resident in HBM, device time of
            exactly K steps (CUDA events on the solve stream), max over ranks.
@@ -15,18 +15,19 @@ roofline   the eigenvalue kernel (k_eig): algorithmic FP64 flops per launch
            (3 per term per bisection step: subtract, divide, add, as in
            Algorithm 3; 6 per term per Newton step, which adds the derivative
            term; 3 per term for the shift choice; 20 per term for the
-           double-double element b) over its event-timed duration, against the
+           double-double element b, or 3 for a standard-precision b under
+           Algorithm 5's gate) over its event-timed duration, against the
            FP64 ALU peak 152 SMs x 4 flop/clk x 2070 MHz.  Also reported: the
            all-FP64 bisection's algorithmic work over the headline form's k_eig
            time (fp64_bisection_equivalent_tflops).
-forms      fp64_newton_gated: fp64_newton with Algorithm 5's precision gates
-           (b in standard precision unless the spike ratio and K_b ask
-           for double-double).
-           fp64_newton (default headline): FP64 throughout, the bracketed
+forms      fp64_newton_gated (default headline): Algorithm 5 -- b in
+           standard precision unless the spike ratio and K_b ask for
+           double-double -- with the bracketed Newton finish, FP64 throughout.
+           fp64_newton: the same with b always in double-double, the bracketed
            Newton finish (same Pick function, bracket and stop test as
            Algorithm 3); fp64: all-FP64 bisection as in Algorithm 3; fp32:
-           FP32 opening bracket then FP64 bisection; fp32_newton.  All four are
-           timed; --form picks the headline.
+           FP32 opening bracket then FP64 bisection; fp32_newton.  All five
+           are timed; --form picks the headline.
 cpu_baseline  the CPU oracle on a bounded sample of eigenpairs of the same
            matrix, on all host cores.
 --impl reference   times the CPU oracle alone (the reference arm).
@@ -92,10 +93,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--form", default="fp64_newton", choices=list(FORMS),
-                   help="headline form: fp64_newton = FP64 with the bracketed Newton finish "
-                        "(default); fp32 = FP32 opening bracket + FP64 bisection; fp64 = "
-                        "all-FP64 bisection (Algorithm 3); fp32_newton")
+    p.add_argument("--form", default="fp64_newton_gated", choices=list(FORMS),
+                   help="headline form: fp64_newton_gated = Algorithm 5's precision gates "
+                        "with the bracketed Newton finish (default); fp64_newton = the same "
+                        "with b always double-double; fp32 = FP32 opening bracket + FP64 "
+                        "bisection; fp64 = all-FP64 bisection (Algorithm 3); fp32_newton")
     p.add_argument("--forms", default=",".join(FORMS),
                    help="comma-separated forms to time beside the headline (default: all)")
     p.add_argument("--no-e2e", action="store_true")
@@ -158,14 +160,18 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
-def eig_kernel_flops(n, ncomp, total_iter, fix_iter, per_eval=3.0):
+def eig_kernel_flops(n, ncomp, total_iter, fix_iter, per_eval=3.0, n_ddb=None):
     """Algorithmic FP64 flops of one k_eig launch (see module docstring).
 
     per_eval: flops per term of one FP64 evaluation of the secular function,
     3 for a bisection step (sub, div, add), 6 for a Newton step (the same
-    plus the derivative term's mul, div, add)."""
+    plus the derivative term's mul, div, add).  n_ddb: None when b is always
+    double-double (20 flops per term); else the number of eigenpairs whose b
+    Algorithm 5's gate sent to double-double, the rest costing 3 flops per
+    term (sub, div, add) for the standard-precision b."""
     terms = n - 2                    # each O(n) pass runs over the other poles
-    return per_eval * terms * (total_iter - fix_iter) + (3.0 + 20.0) * terms * ncomp
+    b = 20.0 * ncomp if n_ddb is None else 3.0 * ncomp + 20.0 * n_ddb
+    return per_eval * terms * (total_iter - fix_iter) + terms * (3.0 * ncomp + b)
 
 
 def cpu_baseline(d, z, alpha, n, seconds):
@@ -235,8 +241,9 @@ def extras(arrowhead, W, dev, stream, flush, args):
         info.update(arrowhead.dpr1_eig(dt, ut, rho, opts=opts, info=True,
                                        out={"lam": lam, "Q": Q}, stream=stream)["info"])
     ms = timed_device(f_dpr1, 3, 1, stream, flush)
+    gated = FORMS[args.form][2] == 1
     fl = eig_kernel_flops(n + 1, info["n_reduced"], info["total_iter"], info["fix_iter"],
-                          per_eval)
+                          per_eval, info["n_ddb"] if gated else None)
     out["dpr1_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                          "k_eig_ms": info["ms_eig"],
                          "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -248,7 +255,8 @@ def extras(arrowhead, W, dev, stream, flush, args):
         info.update(arrowhead.tri_arrow_svd(dt, zt, al, opts=opts, info=True,
                                             out={"s": lam, "U": U, "V": Q}, stream=stream)["info"])
     ms = timed_device(f_svd, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval)
+    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval,
+                          info["n_ddb"] if gated else None)
     out["svd_n8192"] = {"value": n / (ms / 1e3), "unit": "singular triplets/s", "ms_per_step": ms,
                         "k_eig_ms": info["ms_eig"],
                         "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -262,7 +270,8 @@ def extras(arrowhead, W, dev, stream, flush, args):
         info.update(arrowhead.herm_arrow_eig(dt, zt, al, opts=opts, info=True,
                                              out={"lam": lam, "U": Uc}, stream=stream)["info"])
     ms = timed_device(f_herm, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval)
+    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval,
+                          info["n_ddb"] if gated else None)
     out["herm_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                          "k_eig_ms": info["ms_eig"],
                          "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -277,7 +286,8 @@ def extras(arrowhead, W, dev, stream, flush, args):
                                              out={"lam": lam, "X": Q, "Y": Y},
                                              stream=stream)["info"])
     ms = timed_device(f_nsym, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval)
+    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval,
+                          info["n_ddb"] if gated else None)
     out["nsym_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                          "k_eig_ms": info["ms_eig"],
                          "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -452,7 +462,8 @@ def main():
     info = infos[-1]
     eig_ms = float(np.mean([x["ms_eig"] for x in infos]))
     per_eval = 6.0 if FORMS[primary][1] == 1 else 3.0
-    flops = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval)
+    flops = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval,
+                             info["n_ddb"] if FORMS[primary][2] else None)
     achieved = flops / (eig_ms / 1e3) / 1e12
     # the all-FP64 bisection's algorithmic work (its measured step count) over
     # this form's k_eig time: the rate at which the paper's work gets done

@@ -160,13 +160,16 @@ __global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o) {
     const int nfix = S.cnt[C_NFIX];
     const auto R = PolesOf<K>::make(S, m);
     const CtaTeam<8> T{(int)threadIdx.x, red};
+    // k_eig has finished with the stored-pair buffer: one slice per CTA here
+    // (the grid never exceeds k_eig's warp count)
+    double2 *buf = S.wbuf ? S.wbuf + (long long)blockIdx.x * S.wstride : nullptr;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) ticket = atomicAdd(S.cnt + C_WORK2, 1);
         __syncthreads();
         const int w = ticket;
         if (w >= nfix) break;
-        fix_solve_item<K>(R, T, S, S.fixlist[w], o);
+        fix_solve_item<K>(R, T, S, S.fixlist[w], o, buf);
     }
 }
 
@@ -185,8 +188,9 @@ __global__ void __launch_bounds__(256) k_vectors(int n, int n1, const double *__
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int nitems = S.cnt[C_M] + 1 + S.cnt[C_ND];
+    const WarpTeam T{lane};
     for (int item = warp; item < nitems; item += nwarps)
-        vector_item<K>(n, n1, key, spk, z, zrow, alpha, sgn, S, out, item, lane);
+        vector_item<K>(n, n1, key, spk, z, zrow, alpha, sgn, S, out, item, T);
 }
 
 __global__ void k_debug_rcp(int n, const double *x, double *y) {

@@ -202,10 +202,13 @@ __global__ void k_batch_fix_decide(const BatchInst *__restrict__ I, int count,
 
 __global__ void __launch_bounds__(256) k_batch_fix_solve(const BatchInst *__restrict__ I,
                                                          const int2 *fixlist, BatchCtl *ctl,
-                                                         SolveOpts o) {
+                                                         SolveOpts o, double2 *wbuf,
+                                                         long long wstride) {
     __shared__ double red[16];
     __shared__ int ticket;
     const CtaTeam<8> T{(int)threadIdx.x, red};
+    // k_batch_eig has finished with its stored-pair slices: one per CTA here
+    double2 *buf = wbuf ? wbuf + (long long)blockIdx.x * wstride : nullptr;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) ticket = atomicAdd(&ctl->tick_fix, 1);
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(256) k_batch_fix_solve(const BatchInst *__rest
         const int2 ik = fixlist[w];
         const Scratch &S = I[ik.x].S;
         const auto R = PolesOf<KIND_ARROW>::make(S, S.cnt[C_M]);
-        fix_solve_item<KIND_ARROW>(R, T, S, ik.y, o);
+        fix_solve_item<KIND_ARROW>(R, T, S, ik.y, o, buf);
     }
 }
 
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(256) k_batch_vectors(const BatchInst *__restri
         const int i = find_inst(eoff, count, t);
         const BatchInst &B = I[i];
         vector_item<KIND_ARROW>(B.n, B.n1, B.d, B.z, B.z, nullptr, *B.alpha, 1.0, B.S, B.out,
-                                (int)(t - eoff[i]), lane);
+                                (int)(t - eoff[i]), WarpTeam{lane});
         __syncwarp();
     }
 }
@@ -386,7 +389,8 @@ static void enqueue(const Plan &P, cudaStream_t st) {
     if (P.ro.fixup) {
         k_batch_fix_decide<<<g, 256, 0, st>>>(P.d_inst, P.count, P.d_eoff, P.d_fix, P.d_ctl,
                                               P.ro.knu_max);
-        k_batch_fix_solve<<<sms * 4, 256, 0, st>>>(P.d_inst, P.d_fix, P.d_ctl, P.so);
+        k_batch_fix_solve<<<sms * 4, 256, 0, st>>>(P.d_inst, P.d_fix, P.d_ctl, P.so, P.wbuf,
+                                                   P.wstride);
     }
     k_batch_place<<<g, 256, 0, st>>>(P.d_inst, P.count, P.d_eoff);
     k_batch_vectors<<<sms * 16, 256, 0, st>>>(P.d_inst, P.count, P.d_eoff, P.d_ctl);

@@ -391,20 +391,21 @@ static __device__ int fix_decide_item(Kind kind, const Scratch &S, int k, double
 }
 
 // Remedy solve of eigenpair k by a CTA team (all threads of the block call it).
+// buf: the team's slice of stored pairs (or null).
 template <Kind K, class Team>
 __device__ void fix_solve_item(const typename PolesOf<K>::type &R, const Team &T, const Scratch &S,
-                               int k, const SolveOpts &o) {
+                               int k, const SolveOpts &o, double2 *buf = nullptr) {
     const int m = S.cnt[C_M];
     const int f = S.es_flags[k];
     EigResult res;
     if (f & AE_FLAG_NEARZERO) {
-        res = solve_dpr1_shift(R, T, 0.0, o);
+        res = solve_dpr1_shift(R, T, 0.0, o, buf);
     } else if (f & AE_FLAG_OTHERPOLE) {
         const int io = S.es_fixpole[k];
         const int side = io < S.es_pole[k] ? -1 : +1;   // other pole above -> lambda below it
-        res = solve_shifted(R, T, io, side, o);
+        res = solve_shifted(R, T, io, side, o, buf);
     } else {
-        res = solve_dpr1_shift(R, T, S.es_fixshift[k], o);
+        res = solve_dpr1_shift(R, T, S.es_fixshift[k], o, buf);
     }
     // the result must stay in the eigenvalue's interlacing interval
     const double lo = k < m ? R.pole(k) : (K == KIND_DPR1 ? S.prm[P_PLAST] : -INFINITY);
@@ -450,13 +451,14 @@ static __device__ void place_item(const Scratch &S, int t) {
 
 // Helmert-type vector of a run-folded row:
 // (-s_q sum_{l<m} s_l e_l + R_{m-1}^2 e_q) / (R_{m-1} R_m) with the run's spikes s
+template <int STRIDE = 32>
 __device__ __forceinline__ void run_column(const Scratch &S, const double *spk, int row, int lane,
                                            double *col, double sign) {
     const double Rm1 = S.run_R[2 * row], Rm = S.run_R[2 * row + 1];
     const double zq = spk[row];
     const double den = Rm1 * Rm;
     const int s0 = S.run_s0[row], s1 = S.spos[row];
-    for (int s = s0 + lane; s < s1; s += 32) {
+    for (int s = s0 + lane; s < s1; s += STRIDE) {
         const int rq = S.perm[s];
         const double zl = spk[rq];
         if (zl != 0.0) col[rq] = sign * (-(zq * zl) / den);
@@ -464,7 +466,7 @@ __device__ __forceinline__ void run_column(const Scratch &S, const double *spk, 
     if (lane == 0) col[row] = sign * (Rm1 / Rm);
 }
 
-// Output of item `item` (a computed eigenpair, or a deflated row) by one warp:
+// Output of item `item` (a computed eigenpair, or a deflated row) by one team:
 // value, optional shift/mu/diagnostics, and its column(s).  `key`/`spk` are the
 // transformed inputs the reduction saw; z is the caller's spike array (SVD:
 // for the left vectors; HERM: the complex spikes; NSYM: the column spikes,
@@ -474,11 +476,12 @@ __device__ __forceinline__ void run_column(const Scratch &S, const double *spk, 
 // Phi_r |zeta_r| = zeta_r.  NSYM writes the right vectors X = Psi V into V and
 // the left ones Y = Psi^{-1} V into U: x_r = zc_r t_r / ||x||, y_r = zr_r t_r
 // / ||x||, since Psi_r sqrt(zc_r zr_r) = zc_r; then y^T x = 1.
-template <Kind K>
+template <Kind K, class Team>
 __device__ void vector_item(int n, int n1, const double *__restrict__ key,
                             const double *__restrict__ spk, const double *__restrict__ z,
                             const double *__restrict__ zrow, double alpha, double sgn,
-                            const Scratch &S, const Outputs &out, int item, int lane) {
+                            const Scratch &S, const Outputs &out, int item, const Team &T) {
+    const int lane = T.rank;
     constexpr bool CPLX = K == KIND_HERM;
     constexpr bool TWO = K == KIND_NSYM;
     constexpr int RS = CPLX ? 2 : 1;           // doubles per row
@@ -542,21 +545,22 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
         // Pass 1 stores x (HERM, NSYM: the reciprocal t) in the column and sums
         // x^2 in sorted order (so the norm does not depend on the order of the
         // input rows); pass 2 scales in place.
+        double *keep = col;                      // pass-1 values, RS doubles a row
         double s = 0.0;
-        for (int q = lane; q < n1; q += 32) {
+        for (int q = lane; q < n1; q += Team::size) {
             const int r = S.perm[q];
             if (CPLX || TWO) {
                 const double t = recip(r);
-                col[RS * r] = t;
+                keep[RS * r] = t;
                 const double x = spk[r] * t;
                 s = fma(x, x, s);
             } else {
                 const double x = comp(r);
-                col[r] = x;
+                keep[r] = x;
                 s = fma(x, x, s);
             }
         }
-        s = warp_sum(s) + (last_row ? 1.0 : 0.0);
+        s = T.sum(s) + (last_row ? 1.0 : 0.0);
         double inv, scale = 1.0;
         bool stored = true;
         if (isfinite(s) && s > 0x1p-960) {
@@ -565,31 +569,54 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
             // rescale by the largest component to avoid overflow/underflow
             stored = false;
             double xm = last_row ? 1.0 : 0.0;
-            for (int r = lane; r < n1; r += 32) xm = fmax(xm, fabs(comp(r)));
-            xm = warp_max(xm);
+            for (int r = lane; r < n1; r += Team::size) xm = fmax(xm, fabs(comp(r)));
+            xm = T.max(xm);
             scale = 1.0 / xm;
             double s2 = 0.0;
-            for (int q = lane; q < n1; q += 32) {
+            for (int q = lane; q < n1; q += Team::size) {
                 const double x = comp(S.perm[q]) * scale;
                 s2 = fma(x, x, s2);
             }
-            s2 = warp_sum(s2) + (last_row ? scale * scale : 0.0);
+            s2 = T.sum(s2) + (last_row ? scale * scale : 0.0);
             inv = 1.0 / sqrt(s2);
         }
         // DPR1 with rho < 0 solved -M: q ~ (D - lambda)^{-1} u needs a sign flip
         const double vs = (K == KIND_DPR1 && sgn < 0.0) ? -1.0 : 1.0;
-        __syncwarp();
-        for (int r = lane; r < n1; r += 32) {
+        T.sync();
+        int r0 = lane;
+        if (stored && !CPLX && !TWO) {
+            // the common case, four rows a lane at a time so that four loads of
+            // the pass-1 values are in flight (vs = +-1, so x (vs inv) is
+            // bitwise vs x inv)
+            const double f = vs * inv;
+            constexpr int ST = Team::size;
+            for (; r0 + 3 * ST < n1; r0 += 4 * ST) {
+                const double x0 = keep[r0], x1 = keep[r0 + ST], x2 = keep[r0 + 2 * ST],
+                             x3 = keep[r0 + 3 * ST];
+                const double v0 = x0 * f, v1 = x1 * f, v2 = x2 * f, v3 = x3 * f;
+                col[r0] = v0;
+                col[r0 + ST] = v1;
+                col[r0 + 2 * ST] = v2;
+                col[r0 + 3 * ST] = v3;
+                if (ucol) {
+                    ucol[r0] = sv * v0 / key[r0];
+                    ucol[r0 + ST] = sv * v1 / key[r0 + ST];
+                    ucol[r0 + 2 * ST] = sv * v2 / key[r0 + 2 * ST];
+                    ucol[r0 + 3 * ST] = sv * v3 / key[r0 + 3 * ST];
+                }
+            }
+        }
+        for (int r = r0; r < n1; r += Team::size) {
             if (CPLX) {
-                const double t = (stored ? col[2 * r] : recip(r) * scale) * inv;
+                const double t = (stored ? keep[2 * r] : recip(r) * scale) * inv;
                 col[2 * r] = z[2 * r] * t;
                 col[2 * r + 1] = z[2 * r + 1] * t;
             } else if (TWO) {
-                const double t = (stored ? col[r] : recip(r) * scale) * inv;
+                const double t = (stored ? keep[r] : recip(r) * scale) * inv;
                 col[r] = z[r] * t;
                 if (ucol) ucol[r] = zrow[r] * t;
             } else {
-                const double x = stored ? col[r] : comp(r) * scale;
+                const double x = stored ? keep[r] : comp(r) * scale;
                 const double v = vs * x * inv;
                 col[r] = v;
                 if (ucol) ucol[r] = sv * v / key[r];      // u_j = s v_j / d_j
@@ -617,10 +644,10 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
             if (out.dg_flags) out.dg_flags[pos] = AE_FLAG_DEFLATED;
         }
         if (!col) return;
-        for (int r = lane; r < RS * n; r += 32) col[r] = 0.0;
+        for (int r = lane; r < RS * n; r += Team::size) col[r] = 0.0;
         if (TWO && ucol)
-            for (int r = lane; r < n; r += 32) ucol[r] = 0.0;
-        __syncwarp();
+            for (int r = lane; r < n; r += Team::size) ucol[r] = 0.0;
+        T.sync();
         if (S.kind[row] == 1) {
             if (lane == 0) {
                 col[RS * row] = 1.0;
@@ -635,7 +662,7 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
             const double zq = spk[row];
             const double f = -zq / (Rm1 * Rm);
             const int s0 = S.run_s0[row], s1 = S.spos[row];
-            for (int q = s0 + lane; q < s1; q += 32) {
+            for (int q = s0 + lane; q < s1; q += Team::size) {
                 const int rq = S.perm[q];
                 if (spk[rq] == 0.0) continue;
                 if (CPLX) {
@@ -657,12 +684,12 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
                 }
             }
         } else {
-            run_column(S, spk, row, lane, col, 1.0);
+            run_column<Team::size>(S, spk, row, lane, col, 1.0);
         }
         if (K == KIND_TSVD && ucol) {
             // B v = d_r v for a deflated right vector (its last entry is 0)
-            __syncwarp();
-            for (int r = lane; r < n; r += 32) ucol[r] = col[r];
+            T.sync();
+            for (int r = lane; r < n; r += Team::size) ucol[r] = col[r];
         }
     }
 }

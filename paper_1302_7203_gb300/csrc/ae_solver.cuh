@@ -62,6 +62,7 @@ struct WarpTeam {
     __device__ __forceinline__ dd sum(dd v) const { return warp_sum_dd(v); }
     __device__ __forceinline__ double max(double v) const { return warp_max(v); }
     __device__ __forceinline__ double min(double v) const { return warp_min(v); }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
 };
 
 // A CTA of NW warps; `red` points at 2*NW doubles of shared memory.
@@ -115,6 +116,7 @@ struct CtaTeam {
         for (int w = 1; w < NW; ++w) r = fmin(r, red[w]);
         return r;
     }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
 // ---------------------------------------------------------------------------
@@ -405,9 +407,11 @@ struct PassA {
 // DD = false (Algorithm 5's standard precision): plain double differences,
 // quotients and sums, 7 instead of ~21 FP64 instructions a term; the stored
 // pairs are the same values.
+// For a shift that is not a pole (skip < 0), q >= 0 is the number of poles
+// above it, which splits the index range the same way.
 template <bool GERSH = true, bool DD = true, class P, class Team>
 __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift, int skip,
-                                        double wscale, double2 *buf = nullptr) {
+                                        double wscale, double2 *buf = nullptr, int q = -1) {
     dd s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
     int c1 = 0, c2 = 0;
     double pmax = -INFINITY, pmin = INFINITY, up = -INFINITY, lo = INFINITY, wsum = 0.0,
@@ -452,11 +456,12 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
         }
     };
     double dhi;
-    if (skip >= 0) {
-        for (int j = T.rank; j < skip; j += Team::size) add(s1, c1, term(j, dhi));
-        int j = skip + 1 + ((T.rank - (skip + 1)) % Team::size + Team::size) % Team::size;
+    if (skip >= 0 || q >= 0) {
+        const int e1 = skip >= 0 ? skip : q, b2 = skip >= 0 ? skip + 1 : q;
+        for (int j = T.rank; j < e1; j += Team::size) add(s1, c1, term(j, dhi));
+        int j = b2 + ((T.rank - b2) % Team::size + Team::size) % Team::size;
         for (; j < R.m; j += Team::size) add(s2, c2, term(j, dhi));
-        if (buf && skip % Team::size == T.rank) buf[skip] = make_double2(0.0, 0.0);
+        if (buf && skip >= 0 && skip % Team::size == T.rank) buf[skip] = make_double2(0.0, 0.0);
     } else {
         for (int j = T.rank; j < R.m; j += Team::size) {
             const dd t = term(j, dhi);
@@ -596,8 +601,9 @@ __device__ bool fp32_verify(int dir, F64 f64, double l, double r, double &left, 
 // is the right end of a bracket of the computed F of bisection's final width.
 // Trial points, in order of preference:
 //  * after a step that was lengthened to tol and did not change sides, F is
-//    rounding noise there: one jump of twice the estimated noise width
-//    (err / |F'|) towards the zero, then midpoints only;
+//    rounding noise there: a jump of twice the estimated noise width
+//    (err / |F'|) towards the zero, growing 4x while it does not change sides,
+//    then midpoints only;
 //  * the zero of the one-pole model  a + kappa x + beta / (x - pole)  that
 //    matches F and F' at x (kappa = -1 for the shifted inverse's Pick
 //    function, 0 for the DPR1 secular function): the Newton step of a function
@@ -621,7 +627,8 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
     for (;;) {
         double x = 0.5 * (left + right);
         double pend = NAN;          // last model point from the good side
-        bool nudged = false, noisy = false, pside = false;
+        double jump = 0.0;
+        bool nudged = false, noisy = false, jumping = false, pside = false;
         double dF = -1.0, err = 0.0;
         while (right - left > TWO_EPS * fabs(0.5 * (left + right)) && it < max_iter) {
             // after a step lengthened to tol the bracket either closes or F is
@@ -637,10 +644,18 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
             double xn;
             bool nudge = false;
             if (noisy) {
-                xn = mid;
+                if (jumping && pos == pside) {          // the jump stayed on one side
+                    jump *= 4.0;
+                    xn = x + towards * jump;
+                } else {
+                    jumping = false;
+                    xn = mid;
+                }
             } else if (nudged && pos == pside) {        // the lengthened step stayed on one side
                 noisy = true;
-                xn = x + towards * fmax(2.0 * err / fabs(dF), 2.0 * tol);
+                jumping = true;
+                jump = fmax(2.0 * err / fabs(dF), 2.0 * tol);
+                xn = x + towards * jump;
             } else {
                 // one-pole model a + kappa x + beta / (x - pole) through (x, F, F'):
                 // beta = (kappa - F') (x - pole)^2 >= 0
@@ -663,6 +678,7 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
             }
             if (!(xn > left && xn < right)) {
                 nudge = false;
+                jumping = false;
                 xn = (!noisy && pend > left && pend < right) ? pend : mid;
             }
             nudged = nudge;
@@ -851,13 +867,29 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
 // phi on that side; lambda = shift + 1/nu.
 template <class P, class Team>
 __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
-                                      const SolveOpts &o) {
+                                      const SolveOpts &o, double2 *buf = nullptr) {
     EigResult res;
     res.sigma = shift;
     res.pole = -1;
     res.b = NAN;
     res.flags = 0;
-    const PassA A = pass_a(R, T, shift, -1, 1.0);
+    // q = number of poles above the shift: delta_j > 0 exactly for j < q, so
+    // the largest 1/delta_j is 1/delta_{q-1} and the smallest 1/delta_q (the
+    // poles are sorted and the shift is none of them)
+    int q = 0;
+    {
+        int hi = R.m;
+        while (q < hi) {
+            const int mid = (q + hi) >> 1;
+            if (R.pole(mid) > shift) q = mid + 1;
+            else hi = mid;
+        }
+    }
+    const PassA A = pass_a<false>(R, T, shift, -1, 1.0, buf, q);
+    const double pmax = q > 0 ? rcp(R.shifted_dd(q - 1, shift, -1).hi)
+                              : (R.m > 0 ? rcp(R.shifted_dd(R.m - 1, shift, -1).hi) : -INFINITY);
+    const double pmin = q < R.m ? rcp(R.shifted_dd(q, shift, -1).hi)
+                                : (R.m > 0 ? rcp(R.shifted_dd(0, shift, -1).hi) : INFINITY);
     const dd Tn = dd_add(A.P, dd_neg(A.Q));   // a - z^T (D - shift)^{-1} z = -Tn
     res.Kb = (A.P.hi + A.Q.hi) / fabs(Tn.hi);
     if (Tn.hi == 0.0) {                       // numerically singular: lambda = shift
@@ -869,20 +901,25 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
     }
     const double rho = -1.0 / Tn.hi;
     const double usq = A.usq + 1.0;          // ||u||^2
+    // the zero lies within rho ||u||^2 of the outermost pole; when the rank-one
+    // term dominates it sits right at that bound, so the computed bound is
+    // widened by 2^-30 relative for its rounding
     double left, right;
     if (rho > 0.0) {
-        left = fmax(A.pmax, 0.0);
+        left = fmax(pmax, 0.0);
         right = fma(rho, usq, left);
+        right += 0x1p-30 * fabs(right);
     } else {
-        right = fmin(A.pmin, 0.0);
+        right = fmin(pmin, 0.0);
         left = fma(rho, usq, right);
+        left -= 0x1p-30 * fabs(left);
     }
     // rho > 0: phi increases through the zero (phi < 0 below it); rho < 0: phi > 0 below
     const int dir = rho > 0.0 ? -1 : +1;
-    auto PHI = [&](double x) {
-        const double S = secular_sum(R, T, shift, -1, x);
-        return fma(rho, S - rcp(x), 1.0);
+    auto S0 = [&](double x) {
+        return buf ? secular_sum_stored(buf, R.m, T, x) : secular_sum(R, T, shift, -1, x);
     };
+    auto PHI = [&](double x) { return fma(rho, S0(x) - rcp(x), 1.0); };
     // (no FP32 opening here: with a shift next to lambda, nu ~ 1/(lambda - shift)
     // is far outside what a power-of-two rescaled FP32 copy can represent, and
     // these solves are a few per cent of all eigenpairs)
@@ -897,9 +934,9 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
         auto FD = [&](double x, bool need_d, double &dF, double &err) {
             double2 S;
             if (need_d) {
-                S = secular_sum_d(R, T, shift, -1, x);
+                S = buf ? secular_sum_d_stored(buf, R.m, T, x) : secular_sum_d(R, T, shift, -1, x);
             } else {
-                S.x = secular_sum(R, T, shift, -1, x);
+                S.x = S0(x);
                 S.y = 0.0;
             }
             const double rx = rcp(x);
