@@ -16,7 +16,9 @@ roofline   the eigenvalue kernel (k_eig): algorithmic FP64 flops per launch
            Algorithm 3; 6 per term per Newton step, which adds the derivative
            term; 3 per term for the shift choice; 20 per term for the
            double-double element b, or 3 for a standard-precision b under
-           Algorithm 5's gate) over its event-timed duration, against the
+           Algorithm 5's gate; 6 per eigenvector component, which k_eig
+           writes as soon as each eigenvalue is known) over its event-timed
+           duration, against the
            FP64 ALU peak 152 SMs x 4 flop/clk x 2070 MHz.  Also reported: the
            all-FP64 bisection's algorithmic work over the headline form's k_eig
            time (fp64_bisection_equivalent_tflops).
@@ -160,7 +162,7 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
-def eig_kernel_flops(n, ncomp, total_iter, fix_iter, per_eval=3.0, n_ddb=None):
+def eig_kernel_flops(n, ncomp, total_iter, fix_iter, per_eval=3.0, n_ddb=None, vectors=True):
     """Algorithmic FP64 flops of one k_eig launch (see module docstring).
 
     per_eval: flops per term of one FP64 evaluation of the secular function,
@@ -168,10 +170,13 @@ def eig_kernel_flops(n, ncomp, total_iter, fix_iter, per_eval=3.0, n_ddb=None):
     plus the derivative term's mul, div, add).  n_ddb: None when b is always
     double-double (20 flops per term); else the number of eigenpairs whose b
     Algorithm 5's gate sent to double-double, the rest costing 3 flops per
-    term (sub, div, add) for the standard-precision b."""
+    term (sub, div, add) for the standard-precision b.  vectors: the kernel
+    also writes each eigenvector column (Eq. Aeigenvec: 2 subtractions and a
+    division per component, 3 flops more to normalise)."""
     terms = n - 2                    # each O(n) pass runs over the other poles
     b = 20.0 * ncomp if n_ddb is None else 3.0 * ncomp + 20.0 * n_ddb
-    return per_eval * terms * (total_iter - fix_iter) + terms * (3.0 * ncomp + b)
+    vec = 6.0 * (n - 1) * ncomp if vectors else 0.0
+    return per_eval * terms * (total_iter - fix_iter) + terms * (3.0 * ncomp + b) + vec
 
 
 def cpu_baseline(d, z, alpha, n, seconds):
@@ -471,7 +476,7 @@ def main():
     if "fp64" in runs:
         i64 = runs["fp64"][1][-1]
         eq = eig_kernel_flops(n, i64["n_reduced"], i64["total_iter"],
-                              i64["fix_iter"]) / (eig_ms / 1e3) / 1e12
+                              i64["fix_iter"], vectors=True) / (eig_ms / 1e3) / 1e12
     traffic = None
     if (KEIG_TRAFFIC["form"] == primary and KEIG_TRAFFIC["n"] == n
             and KEIG_TRAFFIC["src_sha256"] == csrc_sha256()):

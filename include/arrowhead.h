@@ -388,7 +388,12 @@ int ae_serve_destroy(ae_server *srv);
  * arrow_eig_host -- arrow_eig on HOST buffers: copies d and z to the device,
  * solves, and copies lambda (and V, shift, mu when non-NULL) back, all on
  * `stream`, then synchronises.  Host buffers should be pinned for full
- * copy bandwidth.  Arguments as arrow_eig; V is n x n with ldv = n.
+ * copy bandwidth.  When V is page-locked memory the device can address
+ * (cudaHostAlloc, cudaHostRegister), the solver writes the eigenvector columns
+ * into it directly while it computes (each column staged on the device and
+ * written once), so the 8 n^2-byte transfer overlaps the solve; otherwise V is
+ * computed on the device and copied back after it.  Arguments as arrow_eig;
+ * V is n x n with ldv = n.
  */
 int arrow_eig_host(int n, const double *d_host, const double *z_host, double alpha,
                    double *lambda_host, double *V_host, double *shift_host,
@@ -405,7 +410,7 @@ int arrow_eig_host(int n, const double *d_host, const double *z_host, double alp
  * Arguments, outputs and return codes are those of arrow_eig (opts->profile is
  * ignored).  The solve's scratch lives in one static device array of
  * AE_NOALLOC_SCRATCH_BYTES (4 MiB) that every GPU loading the library holds
- * until the process exits; n is limited to what fits, n <= 21376 (larger n
+ * until the process exits; n is limited to what fits, n <= 20928 (larger n
  * returns AE_ERR_TOO_LARGE without touching the GPU).  The call issues no
  * cudaMalloc/cudaFree and no allocating library routine.
  *  - Its first call on a device looks up the array's device address

@@ -285,7 +285,19 @@ int arrow_eig_host(int n, const double *d_host, const double *z_host, double alp
     cudaStream_t st = (cudaStream_t)stream;
     keep_pool_warm();
     const size_t n1 = (size_t)(n - 1);
-    const size_t vbytes = V_host ? sizeof(double) * (size_t)n * (size_t)n : 0;
+    // V_host in page-locked memory the device can address (cudaHostAlloc /
+    // cudaHostRegister): the solver writes the columns there itself, over the
+    // host link while it computes, instead of a copy after the solve
+    double *V_direct = nullptr;
+    if (V_host) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, V_host) == cudaSuccess &&
+            pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            V_direct = (double *)pa.devicePointer;
+        else
+            cudaGetLastError();     // not registered: clear the lookup's error
+    }
+    const size_t vbytes = (V_host && !V_direct) ? sizeof(double) * (size_t)n * (size_t)n : 0;
     const size_t bytes = 256 * 6 + sizeof(double) * (2 * n1 + 3 * (size_t)n) + vbytes;
     void *base = nullptr;
     cudaError_t e = cudaMallocAsync(&base, bytes, st);
@@ -301,7 +313,7 @@ int arrow_eig_host(int n, const double *d_host, const double *z_host, double alp
     double *dl = take(sizeof(double) * n);
     double *ds = shift_host ? take(sizeof(double) * n) : nullptr;
     double *dm = mu_host ? take(sizeof(double) * n) : nullptr;
-    double *dV = V_host ? take(vbytes) : nullptr;
+    double *dV = V_direct ? V_direct : (V_host ? take(vbytes) : nullptr);
     int status = AE_OK;
     if (n1) {
         e = cudaMemcpyAsync(dd_, d_host, sizeof(double) * n1, cudaMemcpyHostToDevice, st);
@@ -313,7 +325,7 @@ int arrow_eig_host(int n, const double *d_host, const double *z_host, double alp
         status = arrow_eig(n, dd_, dz, alpha, dl, dV, n, ds, dm, opts, info, nullptr, stream);
     if (status == AE_OK) {
         e = cudaMemcpyAsync(lambda_host, dl, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && dV)
+        if (e == cudaSuccess && dV && !V_direct)
             e = cudaMemcpyAsync(V_host, dV, vbytes, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && ds)
             e = cudaMemcpyAsync(shift_host, ds, sizeof(double) * n, cudaMemcpyDeviceToHost, st);

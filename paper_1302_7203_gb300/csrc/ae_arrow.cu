@@ -126,8 +126,11 @@ __global__ void __launch_bounds__(1024) k_post(int n1, const double *__restrict_
 // ---------------------------------------------------------------------------
 // eigenpairs
 // ---------------------------------------------------------------------------
-template <Kind K>
-__global__ void __launch_bounds__(256) k_eig(Scratch S, SolveOpts o) {
+// With va.fused, each warp writes eigenpair k's column right after solving it
+// (pass 1 staged in its stored-pair slice, which the solve no longer needs), at
+// the position k + #(deflated values >= lambda_k) that the placement gives.
+template <Kind K, Kind VK>
+__global__ void __launch_bounds__(256) k_eig(Scratch S, SolveOpts o, VecArgs va) {
     const int lane = threadIdx.x & 31;
     const int m = S.cnt[C_M];
     const int ncomp = m + 1;
@@ -141,6 +144,16 @@ __global__ void __launch_bounds__(256) k_eig(Scratch S, SolveOpts o) {
         k = __shfl_sync(FULL, k, 0);
         if (k >= ncomp) break;
         eig_item<K>(R, T, S, k, o, buf);
+        if (va.fused) {
+            __syncwarp();
+            if (lane == 0) {
+                place_item(S, k);
+                S.pos0[k] = S.pos[k];
+            }
+            __syncwarp();
+            vector_item<VK>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn, S,
+                            va.out, k, T, (double *)buf);
+        }
     }
 }
 
@@ -152,8 +165,10 @@ __global__ void k_fix_decide(Kind kind, Scratch S, double knu_max) {
 
 // Remedy solves: one CTA (8 warps) per listed eigenpair, so that the few
 // eigenpairs that need one still fill the GPU.
-template <Kind K>
-__global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o) {
+// With va.fused the same CTA rewrites the remedied eigenpair's column (its
+// position recorded in pos0, as k_eig does).
+template <Kind K, Kind VK>
+__global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o, VecArgs va) {
     __shared__ double red[16];
     __shared__ int ticket;
     const int m = S.cnt[C_M];
@@ -169,7 +184,18 @@ __global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o) {
         __syncthreads();
         const int w = ticket;
         if (w >= nfix) break;
-        fix_solve_item<K>(R, T, S, S.fixlist[w], o, buf);
+        const int k = S.fixlist[w];
+        fix_solve_item<K>(R, T, S, k, o, buf);
+        if (va.fused) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                place_item(S, k);
+                S.pos0[k] = S.pos[k];
+            }
+            __syncthreads();
+            vector_item<VK>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn, S,
+                            va.out, k, T, (double *)buf);
+        }
     }
 }
 
@@ -178,19 +204,26 @@ __global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o) {
 // ---------------------------------------------------------------------------
 __global__ void k_place(Scratch S) { place_item(S, blockIdx.x * blockDim.x + threadIdx.x); }
 
+// All columns, or with va.fused (k_eig and k_fix_solve wrote the computed
+// ones) only those whose final position differs from the one used then, and
+// the deflated ones; the scalar outputs of every item (K_nu and the remedy
+// flags are known only now).  Staged in the warps' stored-pair slices when
+// there are enough of them.
 template <Kind K>
-__global__ void __launch_bounds__(256) k_vectors(int n, int n1, const double *__restrict__ key,
-                                                 const double *__restrict__ spk,
-                                                 const double *__restrict__ z,
-                                                 const double *__restrict__ zrow, double alpha,
-                                                 double sgn, Scratch S, Outputs out) {
+__global__ void __launch_bounds__(256) k_vectors(VecArgs va, Scratch S) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int nitems = S.cnt[C_M] + 1 + S.cnt[C_ND];
+    const int ncomp = S.cnt[C_M] + 1;
+    const int nitems = ncomp + S.cnt[C_ND];
     const WarpTeam T{lane};
-    for (int item = warp; item < nitems; item += nwarps)
-        vector_item<K>(n, n1, key, spk, z, zrow, alpha, sgn, S, out, item, T);
+    double *stage = (S.wbuf && va.fused) ? (double *)(S.wbuf + (long long)warp * S.wstride)
+                                         : nullptr;
+    for (int item = warp; item < nitems; item += nwarps) {
+        const bool cols = !(va.fused && item < ncomp) || S.pos[item] != S.pos0[item];
+        vector_item<K>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn, S, va.out,
+                       item, T, stage, cols);
+    }
 }
 
 __global__ void k_debug_rcp(int n, const double *x, double *y) {
@@ -248,6 +281,7 @@ static size_t layout(uintptr_t base, int n, Scratch *S) {
     T.es_fixpole = (int *)take(sizeof(int) * nn);
     T.fixlist = (int *)take(sizeof(int) * nn);
     T.pos = (int *)take(sizeof(int) * nn);
+    T.pos0 = (int *)take(sizeof(int) * nn);
     T.wbuf = nullptr;
     T.wstride = 0;
     if (S) *S = T;
@@ -281,7 +315,8 @@ static int sm_count() {
 static int eig_grid(int n) {
     static int per_sm = 0;
     if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eig<KIND_ARROW>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eig<KIND_ARROW, KIND_ARROW>,
+                                                      256, 0);
         if (per_sm <= 0) per_sm = 1;
     }
     const int want = (n + 7) / 8;
@@ -291,20 +326,28 @@ static int eig_grid(int n) {
 
 int eig_grid_warps(int n) { return eig_grid(n) * 8; }
 
-template <Kind K>
-static void launch_eig_kernels(int n, Scratch S, const SolveOpts &so, const RunOpts &ro,
-                               cudaStream_t st) {
+// K: the arrowhead the kernels solve; VK: the kind of the vector epilogue
+// (Hermitian and non-symmetric inputs solve the real arrowhead of their moduli)
+template <Kind K, Kind VK>
+static void launch_pipeline(int n, Scratch S, const SolveOpts &so, const RunOpts &ro,
+                            const VecArgs &va, cudaStream_t st) {
     const int sms = sm_count();
     const int grid = eig_grid(n);
     if (ro.ev[1]) cudaEventRecord(ro.ev[1], st);
-    k_eig<K><<<grid, 256, 0, st>>>(S, so);
+    k_eig<K, VK><<<grid, 256, 0, st>>>(S, so, va);
     if (ro.ev[2]) cudaEventRecord(ro.ev[2], st);
     if (ro.fixup) {
         k_fix_decide<<<(n + 255) / 256, 256, 0, st>>>(K, S, ro.knu_max);
         const int fgrid = n < sms * 4 ? n : sms * 4;
-        k_fix_solve<K><<<fgrid, 256, 0, st>>>(S, so);
+        k_fix_solve<K, VK><<<fgrid, 256, 0, st>>>(S, so, va);
     }
     if (ro.ev[3]) cudaEventRecord(ro.ev[3], st);
+    k_place<<<(n + 255) / 256, 256, 0, st>>>(S);
+    // fused: one warp per stored-pair slice, so every warp can stage
+    int vgrid = (n + 7) / 8;
+    const int vcap = va.fused ? grid : sms * 16;
+    vgrid = vgrid < vcap ? vgrid : vcap;
+    k_vectors<VK><<<vgrid, 256, 0, st>>>(va, S);
 }
 
 cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, double alpha,
@@ -325,7 +368,6 @@ cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, dou
     }
     e = cudaMemsetAsync(S.cnt64, 0, sizeof(unsigned long long) * C64_COUNT, st);
     if (e) return e;
-    const int sms = sm_count();
     if (ro.ev[0]) cudaEventRecord(ro.ev[0], st);
     if (n1 > 0) {
         const int g = (n1 + 255) / 256;
@@ -334,51 +376,27 @@ cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, dou
     }
     k_reduce<<<1, 1024, 0, st>>>(n1, key, spk, S.perm, S);
     SolveOpts so{ro.max_iter, ro.precision, ro.finish, ro.bgate, ro.kb_max};
+    VecArgs va{n, n1, key, spk, z, zrow, alpha, sgn, out, (S.wbuf && out.V) ? 1 : 0};
     switch (kind) {
         case KIND_ARROW:
             k_post<KIND_ARROW><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
-            launch_eig_kernels<KIND_ARROW>(n, S, so, ro, st);
+            launch_pipeline<KIND_ARROW, KIND_ARROW>(n, S, so, ro, va, st);
             break;
         case KIND_DPR1:
             k_post<KIND_DPR1><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, fabs(rho), S);
-            launch_eig_kernels<KIND_DPR1>(n, S, so, ro, st);
+            launch_pipeline<KIND_DPR1, KIND_DPR1>(n, S, so, ro, va, st);
             break;
         case KIND_TSVD:
             k_post<KIND_TSVD><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
-            launch_eig_kernels<KIND_TSVD>(n, S, so, ro, st);
+            launch_pipeline<KIND_TSVD, KIND_TSVD>(n, S, so, ro, va, st);
             break;
         case KIND_HERM:
             k_post<KIND_HERM><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
-            launch_eig_kernels<KIND_ARROW>(n, S, so, ro, st);
+            launch_pipeline<KIND_ARROW, KIND_HERM>(n, S, so, ro, va, st);
             break;
         case KIND_NSYM:
             k_post<KIND_NSYM><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
-            launch_eig_kernels<KIND_ARROW>(n, S, so, ro, st);
-            break;
-    }
-    k_place<<<(n + 255) / 256, 256, 0, st>>>(S);
-    int vgrid = (n + 7) / 8;
-    vgrid = vgrid < sms * 16 ? vgrid : sms * 16;
-    switch (kind) {
-        case KIND_ARROW:
-            k_vectors<KIND_ARROW><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, zrow, alpha, sgn, S,
-                                                        out);
-            break;
-        case KIND_DPR1:
-            k_vectors<KIND_DPR1><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, zrow, alpha, sgn, S,
-                                                       out);
-            break;
-        case KIND_TSVD:
-            k_vectors<KIND_TSVD><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, zrow, alpha, sgn, S,
-                                                       out);
-            break;
-        case KIND_HERM:
-            k_vectors<KIND_HERM><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, zrow, alpha, sgn, S,
-                                                       out);
-            break;
-        case KIND_NSYM:
-            k_vectors<KIND_NSYM><<<vgrid, 256, 0, st>>>(n, n1, key, spk, z, zrow, alpha, sgn, S,
-                                                       out);
+            launch_pipeline<KIND_ARROW, KIND_NSYM>(n, S, so, ro, va, st);
             break;
     }
     if (ro.ev[4]) cudaEventRecord(ro.ev[4], st);

@@ -104,6 +104,8 @@ __global__ void __launch_bounds__(1024) k_batch_prep(const BatchInst *__restrict
     if (threadIdx.x < C_COUNT) S.cnt[threadIdx.x] = 0;
     if (threadIdx.x < C64_COUNT) S.cnt64[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) sflags = 0;
+    // -1: no column written by the remedy pass (see k_batch_fix_solve)
+    for (int k = threadIdx.x; k < B.n; k += blockDim.x) S.pos0[k] = -1;
     __syncthreads();
     int flags = 0;
     for (int r = threadIdx.x; r < n1; r += blockDim.x) {
@@ -216,9 +218,22 @@ __global__ void __launch_bounds__(256) k_batch_fix_solve(const BatchInst *__rest
         const int w = ticket;
         if (w >= ctl->nfix) break;
         const int2 ik = fixlist[w];
-        const Scratch &S = I[ik.x].S;
+        const BatchInst &B = I[ik.x];
+        const Scratch &S = B.S;
         const auto R = PolesOf<KIND_ARROW>::make(S, S.cnt[C_M]);
         fix_solve_item<KIND_ARROW>(R, T, S, ik.y, o, buf);
+        // the remedied column, by this CTA (as the single-instance pipeline
+        // does), at the position it has now; k_batch_vectors skips it unless
+        // the final placement moved it
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            place_item(S, ik.y);
+            S.pos0[ik.y] = S.pos[ik.y];
+        }
+        __syncthreads();
+        if (B.out.V)
+            vector_item<KIND_ARROW>(B.n, B.n1, B.d, B.z, B.z, nullptr, *B.alpha, 1.0, S, B.out,
+                                    ik.y, T, (double *)buf);
     }
 }
 
@@ -242,8 +257,11 @@ __global__ void __launch_bounds__(256) k_batch_vectors(const BatchInst *__restri
         if (t >= total) break;
         const int i = find_inst(eoff, count, t);
         const BatchInst &B = I[i];
+        const int item = (int)(t - eoff[i]);
+        const bool cols = !(item <= B.S.cnt[C_M] && B.S.pos0[item] >= 0 &&
+                            B.S.pos[item] == B.S.pos0[item]);
         vector_item<KIND_ARROW>(B.n, B.n1, B.d, B.z, B.z, nullptr, *B.alpha, 1.0, B.S, B.out,
-                                (int)(t - eoff[i]), WarpTeam{lane});
+                                item, WarpTeam{lane}, nullptr, cols);
         __syncwarp();
     }
 }

@@ -67,6 +67,7 @@ struct Scratch {
     double *es_sigma, *es_mu, *es_lam, *es_b, *es_Kb, *es_Knu, *es_fixshift;
     int *es_pole, *es_iters, *es_flags, *es_fixpole, *fixlist;
     int *pos;       // output position of computed (first m+1) and deflated items
+    int *pos0;      // computed item: the position its column was first written at
     double2 *wbuf;  // optional: one (delta_j, c_j) slice per eig team, wstride apart
     long long wstride;
 };
@@ -80,6 +81,19 @@ struct Outputs {
     double *shift, *mu;
     double *dg_b, *dg_Kb, *dg_Knu;
     int *dg_iters, *dg_flags;
+};
+
+// What the eigenvector epilogue needs (the transformed inputs the reduction
+// saw, the caller's spikes, the outputs).  fused != 0: the eigenvalue kernel
+// writes each column as soon as its eigenvalue is known, staged in the warp's
+// stored-pair slice, and the vector kernel later only rewrites the columns
+// that the remedies or the final placement changed (and the deflated ones).
+struct VecArgs {
+    int n, n1;
+    const double *key, *spk, *z, *zrow;
+    double alpha, sgn;
+    Outputs out;
+    int fused;
 };
 
 struct RunOpts {

@@ -476,11 +476,16 @@ __device__ __forceinline__ void run_column(const Scratch &S, const double *spk, 
 // Phi_r |zeta_r| = zeta_r.  NSYM writes the right vectors X = Psi V into V and
 // the left ones Y = Psi^{-1} V into U: x_r = zc_r t_r / ||x||, y_r = zr_r t_r
 // / ||x||, since Psi_r sqrt(zc_r zr_r) = zc_r; then y^T x = 1.
+// stage: null (pass 1 keeps its values in the output column) or the team's
+// scratch for RS * n1 doubles (the column is then written once, normalised --
+// what an output in host memory needs).  columns = false writes the scalar
+// outputs only.
 template <Kind K, class Team>
 __device__ void vector_item(int n, int n1, const double *__restrict__ key,
                             const double *__restrict__ spk, const double *__restrict__ z,
                             const double *__restrict__ zrow, double alpha, double sgn,
-                            const Scratch &S, const Outputs &out, int item, const Team &T) {
+                            const Scratch &S, const Outputs &out, int item, const Team &T,
+                            double *stage = nullptr, bool columns = true) {
     const int lane = T.rank;
     constexpr bool CPLX = K == KIND_HERM;
     constexpr bool TWO = K == KIND_NSYM;
@@ -490,8 +495,9 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
     const bool last_row = K != KIND_DPR1;     // arrowhead rows have the x_n = -1 entry
     int pos = S.pos[item];
     if (K == KIND_DPR1 && sgn < 0.0) pos = n - 1 - pos;   // -M's order reversed
-    double *col = out.V ? out.V + (size_t)pos * out.ldv : nullptr;
-    double *ucol = ((K == KIND_TSVD || TWO) && out.U) ? out.U + (size_t)pos * out.ldu : nullptr;
+    double *col = (out.V && columns) ? out.V + (size_t)pos * out.ldv : nullptr;
+    double *ucol = ((K == KIND_TSVD || TWO) && out.U && columns) ? out.U + (size_t)pos * out.ldu
+                                                                   : nullptr;
     if (item < ncomp) {
         const int k = item;
         const double sig = S.es_sigma[k], mu = S.es_mu[k];
@@ -545,7 +551,7 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
         // Pass 1 stores x (HERM, NSYM: the reciprocal t) in the column and sums
         // x^2 in sorted order (so the norm does not depend on the order of the
         // input rows); pass 2 scales in place.
-        double *keep = col;                      // pass-1 values, RS doubles a row
+        double *keep = stage ? stage : col;      // pass-1 values, RS doubles a row
         double s = 0.0;
         for (int q = lane; q < n1; q += Team::size) {
             const int r = S.perm[q];

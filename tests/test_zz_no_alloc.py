@@ -72,7 +72,7 @@ def test_noalloc_matches_arrow_eig_on_two_calls(ae):
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(ae):
-    n = 21377                                       # first order that does not fit
+    n = 20929                                       # first order that does not fit
     st = ae.lib().arrow_eig_noalloc(n, ctypes.c_void_p(1), ctypes.c_void_p(1), 0.0,
                                     ctypes.c_void_p(1), None, n, None, None, None, None, None,
                                     None)
