@@ -57,12 +57,12 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size k_eig
-# launch (graded n = 16384, fp64_newton form; a 1-pass capture), with the hash
+# launch (graded n = 16384, fp64_newton_gated form; a 1-pass capture), with the hash
 # of the CUDA sources it was measured on.  The bench reports it as the
 # roofline's traffic only while the form, n and sources match.
-KEIG_TRAFFIC = {"form": "fp64_newton", "n": 16384,
-                "read": 13191656448, "write": 4301616384,
-                "src_sha256": "3edfa919f806ac5e7b79055fe17471d4e2e97959d4b4815e68972ee6be2352c2"}
+KEIG_TRAFFIC = {"form": "fp64_newton_gated", "n": 16384,
+                "read": 15407848704, "write": 8537173760,
+                "src_sha256": "f90641df193af4a00820b0fdddc75f6f34ad68e5d64c03e68ac049c71df8480c"}
 
 
 def csrc_sha256():
@@ -484,8 +484,9 @@ def main():
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
             "traffic_note": "bytes per k_eig launch: the per-warp stored (delta_j, "
-                            "zeta_j^2/delta_j) pairs, written once per eigenpair and "
-                            "re-read by each FP64 evaluation",
+                            "zeta_j^2/delta_j) pairs (written once per eigenpair, re-read "
+                            "by each FP64 evaluation), the staged eigenvector column and "
+                            "the n x n V written once",
             "kernel": "k_eig", "kernel_ms": eig_ms,
             "fp64_bisection_equivalent_tflops": eq,
             "peak_note": "FP64 ALU: 152 SMs x 4 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)"}

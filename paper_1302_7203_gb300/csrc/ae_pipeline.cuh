@@ -126,11 +126,17 @@ __device__ __forceinline__ double block_max(double v, double *sh) {
     __syncthreads();
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
-    double r = sh[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
-    return r;
+    if (threadIdx.x == 0) {
+        double r = sh[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+        sh[0] = r;
+    }
+    __syncthreads();
+    return sh[0];
 }
 
+// (the warp partials are combined by thread 0 alone and broadcast: on the one
+// SM a single-CTA kernel runs on, every redundant FP64 instruction counts)
 __device__ __forceinline__ dd block_sum_dd(dd v, double *sh) {
     v = warp_sum_dd(v);
     __syncthreads();
@@ -139,9 +145,28 @@ __device__ __forceinline__ dd block_sum_dd(dd v, double *sh) {
         sh[32 + (threadIdx.x >> 5)] = v.lo;
     }
     __syncthreads();
-    dd r = {sh[0], sh[32]};
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = dd_add(r, dd{sh[w], sh[32 + w]});
-    return r;
+    if (threadIdx.x == 0) {
+        dd r = {sh[0], sh[32]};
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = dd_add(r, dd{sh[w], sh[32 + w]});
+        sh[0] = r.hi;
+        sh[32] = r.lo;
+    }
+    __syncthreads();
+    return dd{sh[0], sh[32]};
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = sh[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+        sh[0] = r;
+    }
+    __syncthreads();
+    return sh[0];
 }
 
 // Kind-specific arrowhead data after the reduction, then the FP32 copies
@@ -224,7 +249,7 @@ __device__ void post_block(int n1, const double *__restrict__ d, const double *_
     __syncthreads();
     double zsum = 0.0;
     for (int j = threadIdx.x; j < m; j += blockDim.x) zsum += S.pz[j];
-    zsum = block_sum_dd(dd{zsum, 0.0}, sh).hi;
+    zsum = block_sum(zsum, sh);
     if (threadIdx.x == 0) S.prm[P_ZSUM] = zsum;
     // FP32 copies: keys and spike^2 scaled by powers of two so that the
     // largest of each is O(1)
