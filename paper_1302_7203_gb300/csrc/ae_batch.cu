@@ -65,6 +65,7 @@ struct SubWarpTeam {
         for (int o = W / 2; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(mask, v, o));
         return v;
     }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
 };
 
 struct BatchInst {
@@ -159,11 +160,26 @@ __device__ __forceinline__ void batch_unit(const BatchInst &B, long long unit_in
     const int k = (int)(unit_in_inst * EPW) + g;
     const auto R = PolesOf<KIND_ARROW>::make(B.S, m);
     double2 *tb = buf ? buf + g * stride : nullptr;
+    // the solve, then (with vectors and a stored-pair slice) the column at its
+    // position as the single-instance k_eig writes it
+    auto run = [&](const auto &T) {
+        eig_item<KIND_ARROW>(R, T, B.S, k, o, tb);
+        if (B.out.V && tb) {
+            T.sync();
+            if (T.rank == 0) {
+                place_item(B.S, k);
+                B.S.pos0[k] = B.S.pos[k];
+            }
+            T.sync();
+            vector_item<KIND_ARROW>(B.n, B.n1, B.d, B.z, B.z, nullptr, *B.alpha, 1.0, B.S,
+                                    B.out, k, T, (double *)tb);
+        }
+    };
     if constexpr (W == 32) {
-        if (k <= m) eig_item<KIND_ARROW>(R, WarpTeam{lane}, B.S, k, o, tb);
+        if (k <= m) run(WarpTeam{lane});
     } else {
         const unsigned mask = ((1u << W) - 1u) << (lane & ~(W - 1));
-        if (k <= m) eig_item<KIND_ARROW>(R, SubWarpTeam<W>{lane & (W - 1), mask}, B.S, k, o, tb);
+        if (k <= m) run(SubWarpTeam<W>{lane & (W - 1), mask});
     }
 }
 
@@ -202,38 +218,39 @@ __global__ void k_batch_fix_decide(const BatchInst *__restrict__ I, int count,
     if (fix_decide_item(KIND_ARROW, I[i].S, k, knu_max)) fixlist[atomicAdd(&ctl->nfix, 1)] = {i, k};
 }
 
+// One warp per remedied eigenpair (remedies are many in a batch of small
+// instances), on the warp's first stored-pair slice; the warp also rewrites the
+// remedied column, which k_batch_vectors then skips unless the final placement
+// moved it.
 __global__ void __launch_bounds__(256) k_batch_fix_solve(const BatchInst *__restrict__ I,
                                                          const int2 *fixlist, BatchCtl *ctl,
                                                          SolveOpts o, double2 *wbuf,
                                                          long long wstride) {
-    __shared__ double red[16];
-    __shared__ int ticket;
-    const CtaTeam<8> T{(int)threadIdx.x, red};
-    // k_batch_eig has finished with its stored-pair slices: one per CTA here
-    double2 *buf = wbuf ? wbuf + (long long)blockIdx.x * wstride : nullptr;
+    const int lane = threadIdx.x & 31;
+    const WarpTeam T{lane};
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    double2 *buf = wbuf ? wbuf + gw * 4 * wstride : nullptr;
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) ticket = atomicAdd(&ctl->tick_fix, 1);
-        __syncthreads();
-        const int w = ticket;
+        int w = 0;
+        if (lane == 0) w = atomicAdd(&ctl->tick_fix, 1);
+        w = __shfl_sync(FULL, w, 0);
         if (w >= ctl->nfix) break;
         const int2 ik = fixlist[w];
         const BatchInst &B = I[ik.x];
         const Scratch &S = B.S;
         const auto R = PolesOf<KIND_ARROW>::make(S, S.cnt[C_M]);
         fix_solve_item<KIND_ARROW>(R, T, S, ik.y, o, buf);
-        // the remedied column, by this CTA (as the single-instance pipeline
-        // does), at the position it has now; k_batch_vectors skips it unless
-        // the final placement moved it
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            place_item(S, ik.y);
-            S.pos0[ik.y] = S.pos[ik.y];
-        }
-        __syncthreads();
-        if (B.out.V)
+        __syncwarp();
+        if (B.out.V && buf) {
+            if (lane == 0) {
+                place_item(S, ik.y);
+                S.pos0[ik.y] = S.pos[ik.y];
+            }
+            __syncwarp();
             vector_item<KIND_ARROW>(B.n, B.n1, B.d, B.z, B.z, nullptr, *B.alpha, 1.0, S, B.out,
                                     ik.y, T, (double *)buf);
+        }
+        __syncwarp();
     }
 }
 
@@ -407,8 +424,8 @@ static void enqueue(const Plan &P, cudaStream_t st) {
     if (P.ro.fixup) {
         k_batch_fix_decide<<<g, 256, 0, st>>>(P.d_inst, P.count, P.d_eoff, P.d_fix, P.d_ctl,
                                               P.ro.knu_max);
-        k_batch_fix_solve<<<sms * 4, 256, 0, st>>>(P.d_inst, P.d_fix, P.d_ctl, P.so, P.wbuf,
-                                                   P.wstride);
+        k_batch_fix_solve<<<batch_eig_grid(), 256, 0, st>>>(P.d_inst, P.d_fix, P.d_ctl, P.so,
+                                                             P.wbuf, P.wstride);
     }
     k_batch_place<<<g, 256, 0, st>>>(P.d_inst, P.count, P.d_eoff);
     k_batch_vectors<<<sms * 16, 256, 0, st>>>(P.d_inst, P.count, P.d_eoff, P.d_ctl);

@@ -415,7 +415,8 @@ static __device__ int fix_decide_item(Kind kind, const Scratch &S, int k, double
     return remedy;
 }
 
-// Remedy solve of eigenpair k by a CTA team (all threads of the block call it).
+// Remedy solve of eigenpair k by a team (a CTA in the single-instance pipeline,
+// a warp in the batched one); all of its threads call it.
 // buf: the team's slice of stored pairs (or null).
 template <Kind K, class Team>
 __device__ void fix_solve_item(const typename PolesOf<K>::type &R, const Team &T, const Scratch &S,
@@ -436,7 +437,7 @@ __device__ void fix_solve_item(const typename PolesOf<K>::type &R, const Team &T
     const double lo = k < m ? R.pole(k) : (K == KIND_DPR1 ? S.prm[P_PLAST] : -INFINITY);
     const double hi = k > 0 ? R.pole(k - 1) : INFINITY;
     const bool ok = (res.lam >= lo && res.lam <= hi) && isfinite(res.lam);
-    if (threadIdx.x == 0) {
+    if (T.rank == 0) {
         if (ok) {
             // b and K_b stay those of Algorithm 1's shift pole
             res.b = S.es_b[k];

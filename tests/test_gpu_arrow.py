@@ -175,6 +175,23 @@ def test_host_entry_point_matches_device(ae):
     np.testing.assert_array_equal(h["V"].numpy(), g["V"])
 
 
+@pytest.mark.parametrize("finish", [0, 1])
+def test_host_entry_point_writes_pinned_V_directly(ae, finish):
+    # page-locked V: the kernels store the columns into host memory during the
+    # solve; pageable V: solved on the device and copied back.  Same bits.
+    d, z, a = W.graded_arrow(3000, seed=6)
+    n = len(d) + 1
+    o = ae.default_opts(finish=finish, bgate=1)
+    g = gpu_solve(ae, d, z, a, opts=o)
+    pinned = {"lam": torch.empty(n, dtype=torch.float64).pin_memory(),
+              "V": torch.full((n, n), np.nan, dtype=torch.float64).pin_memory()}
+    hp = ae.arrow_eig_host(d, z, a, opts=o, out=pinned)
+    hq = ae.arrow_eig_host(d, z, a, opts=o)
+    for h in (hp, hq):
+        np.testing.assert_array_equal(h["lam"].numpy(), g["lam"])
+        np.testing.assert_array_equal(h["V"].numpy(), g["V"])
+
+
 def test_invalid_input_reported(ae):
     d = np.array([1.0, np.nan, 0.5])
     z = np.ones(3)

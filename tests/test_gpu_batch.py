@@ -57,22 +57,31 @@ def test_batch_parity_against_oracle(ae, graph):
 
 
 def test_batch_equals_single_solves(ae):
+    # the same arithmetic on the same team shape gives the same bits: instances
+    # solved by 32-lane teams match arrow_eig exactly, except the remedied pairs
+    # (a CTA team re-solves them in arrow_eig, a warp in the batch), which, like
+    # the instances on narrower teams, agree within the tolerance
     inst = small_batch(count=24, lo=8, hi=2000, seed=5)
     B = ae.Batch(inst)
     B.run()
     torch.cuda.synchronize()
+    remedy = ae.FLAG_NEARZERO | ae.FLAG_OTHERPOLE | ae.FLAG_DPR1SHIFT
+    n_exact = 0
     for i, (d, z, a) in enumerate(inst):
         n = len(d) + 1
-        r = ae.arrow_eig(torch.as_tensor(d, device="cuda"), torch.as_tensor(z, device="cuda"), a)
+        r = ae.arrow_eig(torch.as_tensor(d, device="cuda"), torch.as_tensor(z, device="cuda"), a,
+                         diag=True)
         lam1, V1 = r["lam"].cpu().numpy(), r["V"].cpu().numpy()
+        fixed = (r["diag"]["flags"].cpu().numpy() & remedy) != 0
         lamb, Vb = B.lam(i).cpu().numpy(), B.V(i).cpu().numpy()
+        tol = 10 * n * 2.0 ** -53
+        assert np.all(np.abs(lamb - lam1) <= tol * np.abs(lam1))
+        assert np.all(np.abs(Vb - V1) <= tol * np.abs(V1) + 1e-300)
         if ae.lib().ae_team_width(n) == 32:
-            np.testing.assert_array_equal(lamb, lam1)
-            np.testing.assert_array_equal(Vb, V1)
-        else:
-            tol = 10 * n * 2.0 ** -53
-            assert np.all(np.abs(lamb - lam1) <= tol * np.abs(lam1))
-            assert np.all(np.abs(Vb - V1) <= tol * np.abs(V1) + 1e-300)
+            np.testing.assert_array_equal(lamb[~fixed], lam1[~fixed])
+            np.testing.assert_array_equal(Vb[:, ~fixed], V1[:, ~fixed])
+            n_exact += 1
+    assert n_exact > 0
     B.close()
 
 
