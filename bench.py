@@ -28,8 +28,9 @@ forms      fp64_newton_gated (default headline): Algorithm 5 -- b in
            fp64_newton: the same with b always in double-double, the bracketed
            Newton finish (same Pick function, bracket and stop test as
            Algorithm 3); fp64: all-FP64 bisection as in Algorithm 3; fp32:
-           FP32 opening bracket then FP64 bisection; fp32_newton.  All five
-           are timed; --form picks the headline.
+           FP32 opening bracket then FP64 bisection; fp32_newton and
+           fp32_newton_gated (the Newton forms after an FP32 opening bracket).
+           All six are timed; --form picks the headline.
 cpu_baseline  the CPU oracle on a bounded sample of eigenpairs of the same
            matrix, on all host cores.
 --impl reference   times the CPU oracle alone (the reference arm).
@@ -80,7 +81,8 @@ def csrc_sha256():
 
 # solver forms: (ae_opts.precision, ae_opts.finish, ae_opts.bgate)
 FORMS = {"fp32": (1, 0, 0), "fp64": (0, 0, 0), "fp32_newton": (1, 1, 0),
-         "fp64_newton": (0, 1, 0), "fp64_newton_gated": (0, 1, 1)}
+         "fp64_newton": (0, 1, 0), "fp64_newton_gated": (0, 1, 1),
+         "fp32_newton_gated": (1, 1, 1)}
 
 
 def form_opts(arrowhead, form, **kw):
@@ -99,7 +101,8 @@ def parse():
                    help="headline form: fp64_newton_gated = Algorithm 5's precision gates "
                         "with the bracketed Newton finish (default); fp64_newton = the same "
                         "with b always double-double; fp32 = FP32 opening bracket + FP64 "
-                        "bisection; fp64 = all-FP64 bisection (Algorithm 3); fp32_newton")
+                        "bisection; fp64 = all-FP64 bisection (Algorithm 3); fp32_newton; "
+                        "fp32_newton_gated")
     p.add_argument("--forms", default=",".join(FORMS),
                    help="comma-separated forms to time beside the headline (default: all)")
     p.add_argument("--no-e2e", action="store_true")
@@ -410,13 +413,13 @@ def main():
         return
     import torch
     import torch.distributed as dist
-    from paper_1302_7203_gb300 import arrowhead, build, workloads as W
+    from paper_1302_7203_gb300 import arrowhead, build, shard, workloads as W
     build.build()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = args.n
-    d, z, alpha = W.graded_arrow(n, seed=1 + rank)
+    d, z, alpha = W.graded_arrow(n, seed=shard.rank_seed(1, rank))
     dev = torch.device("cuda", local)
     dt = torch.as_tensor(d, device=dev)
     zt = torch.as_tensor(z, device=dev)
@@ -452,9 +455,7 @@ def main():
             dist.barrier()
         total = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
         if world > 1:
-            t = torch.tensor([total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+            total = shard.max_over_ranks(total, device=dev)
         return total, infos, clk
 
     primary = args.form
@@ -507,9 +508,7 @@ def main():
                                      stream=stream)
         te = time.perf_counter() - t0
         if world > 1:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+            te = shard.max_over_ranks(te, device=dev)
         e2e = {"value": world * n * ne / te, "unit": UNIT,
                "h2d_bytes_per_step": 2 * (n - 1) * 8, "d2h_bytes_per_step": (n + n * n) * 8}
 
