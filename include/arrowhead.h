@@ -7,7 +7,8 @@
  * the solver shifts to the nearest pole d_i (Algorithm 1), forms the inverse of
  * the shifted arrowhead (Eq. invAi) with its one cancellation-prone element b
  * (Eq. b_ob) in double-double arithmetic (Theorem 6), finds that inverse's
- * extreme eigenvalue nu by bisection (Algorithm 3), and returns
+ * extreme eigenvalue nu by bisection (Algorithm 3, or a bracketed Newton
+ * finish on the same function; ae_opts.finish), and returns
  * lambda = d_i + 1/nu with the eigenvector of Eq. (eigenvecAi) / Algorithm 4.
  * Eigenvalues whose shifted value cancels (the special cases after Theorem C1)
  * are recomputed from the inverse of A (Remark 1); eigenvalues with a large
@@ -30,6 +31,9 @@
  *    reported in the return value as well; with info == NULL the call does
  *    not synchronise and such conditions show up only as NaN outputs.
  *  - No C++ exception crosses this interface.
+ *  - Range: the solve squares spikes and shifted differences in double
+ *    precision, so entries must lie between about 2^-500 and 2^500 in
+ *    magnitude; scale A by a power of two first when they do not (exact).
  */
 #ifndef ARROWHEAD_H
 #define ARROWHEAD_H

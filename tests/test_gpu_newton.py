@@ -170,3 +170,18 @@ def test_newton_batched(ae):
         assert_parity(B.lam(i).cpu().numpy(), B.V(i).cpu().numpy(), oracle.arrow_eig(d, z, a),
                       len(d) + 1, what=f"newton batch instance {i}")
     B.close()
+
+
+@pytest.mark.parametrize("e", [-400, -300, 300, 400])
+@pytest.mark.parametrize("form", [(0, 0, 0), (0, 1, 1), (1, 1, 0)])
+def test_extreme_power_of_two_scaling(ae, e, form):
+    # A -> 2^e A scales every eigenvalue by 2^e and leaves the vectors, exactly,
+    # as long as the squares the solve forms (zeta^2, delta^2, 1/zeta_i^2) stay
+    # in range: here |entries| from 2^-450 to 2^400
+    d, z, a = W.graded_arrow(300, seed=23)
+    o = ae.default_opts(precision=form[0], finish=form[1], bgate=form[2])
+    g0 = solve(ae, d, z, a, o)
+    s = 2.0 ** e
+    g1 = solve(ae, d * s, z * s, a * s, o)
+    np.testing.assert_array_equal(g1["lam"], g0["lam"] * s)
+    np.testing.assert_array_equal(g1["V"], g0["V"])
