@@ -368,6 +368,14 @@ def serve_sweep(arrowhead, W, dev, count, opts):
     return res
 
 
+def workload_config(n, form, world):
+    """The `config` of both arms' JSON lines (the reference arm times a sample of
+    the same workload, said in its cpu_baseline.sample)."""
+    return {"workload": f"graded arrowhead n={n}: all eigenpairs + full V",
+            "n": n, "form": form, "l2": "512 MiB write between steps (L2 flush)",
+            "parallelism": f"{world} independent instances"}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle, timed on the host cores."""
     if rank != 0:
@@ -393,11 +401,11 @@ def run_reference(args, rank, world):
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 (double-double oracle)",
             "data": "synthetic",
-            "config": {"workload": f"graded arrowhead n={n} (seed 1), sampled eigenpairs "
-                                   "with vectors", "n": n},
+            "config": workload_config(n, args.form, world),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.threads(),
                              "kind": "oracle",
-                             "sample": f"{per_step} eigenpairs per step of {n}"},
+                             "sample": f"{per_step} evenly spaced eigenpairs (with vectors) "
+                                       f"per step of the {n}; double-double oracle"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -537,10 +545,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"graded arrowhead n={n}: all eigenpairs + full V",
-                           "n": n, "form": primary,
-                           "l2": "512 MiB write between steps (L2 flush)",
-                           "parallelism": f"{world} independent instances"},
+                "config": workload_config(n, primary, world),
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
                 "max_err_neps": err, "variants": variants, "extras": extra,
                 "clocks": clk.summary(), "gpu_launches": LAUNCHES_PER_STEP * args.steps,
