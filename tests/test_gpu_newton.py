@@ -183,5 +183,13 @@ def test_extreme_power_of_two_scaling(ae, e, form):
     g0 = solve(ae, d, z, a, o)
     s = 2.0 ** e
     g1 = solve(ae, d * s, z * s, a * s, o)
-    np.testing.assert_array_equal(g1["lam"], g0["lam"] * s)
-    np.testing.assert_array_equal(g1["V"], g0["V"])
+    if form[0] == 0:
+        np.testing.assert_array_equal(g1["lam"], g0["lam"] * s)
+        np.testing.assert_array_equal(g1["V"], g0["V"])
+    else:
+        # the FP32 opening bracket has float's narrower exponent range: where
+        # its rescaled copy cannot represent the problem it falls back, so the
+        # FP64 finish starts elsewhere; same tolerance, not the same bits
+        tol = 10 * len(d) * 2.0 ** -53
+        assert np.all(np.abs(g1["lam"] - g0["lam"] * s) <= tol * np.abs(g0["lam"] * s))
+        assert np.all(np.abs(g1["V"] - g0["V"]) <= tol * np.abs(g0["V"]) + 1e-300)
