@@ -617,23 +617,29 @@ __device__ bool fp32_verify(int dir, F64 f64, double l, double r, double &left, 
 // the search resumes from the known-good end.  Returns the number of FP64
 // evaluations; `fell_back` reports a failed check.
 // ---------------------------------------------------------------------------
+// F' is evaluated (3 more FP64 instructions a term) only when the last step
+// was longer than 2^-26 |x|: after a shorter one the previous F' is within
+// that relative distance of the current one, enough for a step whose own
+// length is below 2^-26 |x|.  dF0 (finite): an estimate of F' at the start that
+// is that good already (the caller's bracket is that tight), so the first
+// evaluation skips F' too.
 template <class FD>
 __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, double kappa,
                                              double gl, double gr, bool lv, bool rv,
                                              int max_iter, double &left, double &right,
-                                             bool &fell_back) {
+                                             bool &fell_back, double dF0 = NAN) {
     int it = 0;
     fell_back = false;
+    bool need_d = !isfinite(dF0);
+    double dF = need_d ? -1.0 : dF0;
     for (;;) {
         double x = 0.5 * (left + right);
         double pend = NAN;          // last model point from the good side
         double jump = 0.0;
         bool nudged = false, noisy = false, jumping = false, pside = false;
-        double dF = -1.0, err = 0.0;
+        double err = 0.0;
         while (right - left > TWO_EPS * fabs(0.5 * (left + right)) && it < max_iter) {
-            // after a step lengthened to tol the bracket either closes or F is
-            // noise there: F' is not needed (the previous one serves)
-            const double F = fd(x, !nudged, dF, err);
+            const double F = fd(x, need_d, dF, err);
             ++it;
             const bool pos = F > 0.0;
             if (pos) { left = x; lv = true; }
@@ -683,8 +689,10 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
             }
             nudged = nudge;
             pside = pos;
+            need_d = !(fabs(xn - x) < 0x1p-26 * fabs(x));
             x = xn;
         }
+        need_d = true;
         if (lv && rv) break;
         if (!lv) {
             ++it;
@@ -818,8 +826,17 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                 res.flags |= 64;
             }
         }
+        // a bracket this tight means all of F's weight sits at its nearest pole
+        // to that accuracy: F'(x) = -1 - W / (x - pole)^2 is the first F'
+        double dF0 = NAN;
+        const double xm = 0.5 * (left + right);
+        if (right - left < 0x1p-26 * fabs(xm)) {
+            const double dx = xm - pole;
+            dF0 = -1.0 - c * (A.usq + 1.0) / (dx * dx);
+        }
         bool fb;
-        it = newton_finish(FD, side, pole, -1.0, gl, gr, lv, rv, o.max_iter, left, right, fb);
+        it = newton_finish(FD, side, pole, -1.0, gl, gr, lv, rv, o.max_iter, left, right, fb,
+                           dF0);
         if (fb) res.flags |= 64;
     } else {
         // Gershgorin bracket of Algorithm 3 for the inverse: diagonal {1/delta_j, 0},
