@@ -12,9 +12,9 @@ value      eigenpairs/s of the whole job, inputs resident in HBM, device time of
 e2e        the same metric through arrow_eig_host: pinned host d, z in, lambda
            and V (2 GiB) out, copies inside the timed region.
 roofline   the eigenvalue kernel (k_eig): algorithmic FP64 flops per launch
-           (3 per term per bisection step: subtract, divide, add, as in
-           Algorithm 3; 6 per term per Newton step, which adds the derivative
-           term; 3 per term for the shift choice; 20 per term for the
+           (3 per term per evaluation of the secular function: subtract,
+           divide, add, as in Algorithm 3; 3 more per Newton evaluation that
+           forms the derivative; 3 per term for the shift choice; 20 per term for the
            double-double element b, or 3 for a standard-precision b under
            Algorithm 5's gate; 6 per eigenvector component, which k_eig
            writes as soon as each eigenvalue is known) over its event-timed
@@ -165,21 +165,22 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
-def eig_kernel_flops(n, ncomp, total_iter, fix_iter, per_eval=3.0, n_ddb=None, vectors=True):
+def eig_kernel_flops(n, ncomp, total_iter, fix_iter, n_ddb=None, total_deriv=0, vectors=True):
     """Algorithmic FP64 flops of one k_eig launch (see module docstring).
 
-    per_eval: flops per term of one FP64 evaluation of the secular function,
-    3 for a bisection step (sub, div, add), 6 for a Newton step (the same
-    plus the derivative term's mul, div, add).  n_ddb: None when b is always
-    double-double (20 flops per term); else the number of eigenpairs whose b
-    Algorithm 5's gate sent to double-double, the rest costing 3 flops per
-    term (sub, div, add) for the standard-precision b.  vectors: the kernel
-    also writes each eigenvector column (Eq. Aeigenvec: 2 subtractions and a
-    division per component, 3 flops more to normalise)."""
+    Per term: 3 flops for the shift choice (Algorithm 1's midpoint test); 20
+    for the double-double b, or 3 (subtract, divide, add) for a standard one
+    where Algorithm 5's gate kept it (n_ddb = the eigenpairs it sent to
+    double-double; None: all double-double); 3 per FP64 evaluation of the
+    secular function (subtract, divide, add, as in Algorithm 3) and 3 more per
+    Newton evaluation that also formed the derivative (total_deriv).  vectors:
+    6 flops per eigenvector component (Eq. Aeigenvec: 2 subtractions and a
+    division; square, add and scale to normalise), which k_eig writes."""
     terms = n - 2                    # each O(n) pass runs over the other poles
     b = 20.0 * ncomp if n_ddb is None else 3.0 * ncomp + 20.0 * n_ddb
     vec = 6.0 * (n - 1) * ncomp if vectors else 0.0
-    return per_eval * terms * (total_iter - fix_iter) + terms * (3.0 * ncomp + b) + vec
+    evals = 3.0 * (total_iter - fix_iter) + 3.0 * total_deriv
+    return terms * (evals + 3.0 * ncomp + b) + vec
 
 
 def cpu_baseline(d, z, alpha, n, seconds):
@@ -236,7 +237,6 @@ def extras(arrowhead, W, dev, stream, flush, args):
     set and a serving sweep."""
     import torch
     out = {}
-    per_eval = 6.0 if FORMS[args.form][1] == 1 else 3.0
     opts = form_opts(arrowhead, args.form, profile=1)
     n = 8192
     d, u, rho = W.uniform_dpr1(n, seed=3)
@@ -251,7 +251,7 @@ def extras(arrowhead, W, dev, stream, flush, args):
     ms = timed_device(f_dpr1, 3, 1, stream, flush)
     gated = FORMS[args.form][2] == 1
     fl = eig_kernel_flops(n + 1, info["n_reduced"], info["total_iter"], info["fix_iter"],
-                          per_eval, info["n_ddb"] if gated else None)
+                          info["n_ddb"] if gated else None, info["total_deriv"])
     out["dpr1_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                          "k_eig_ms": info["ms_eig"],
                          "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -263,8 +263,8 @@ def extras(arrowhead, W, dev, stream, flush, args):
         info.update(arrowhead.tri_arrow_svd(dt, zt, al, opts=opts, info=True,
                                             out={"s": lam, "U": U, "V": Q}, stream=stream)["info"])
     ms = timed_device(f_svd, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval,
-                          info["n_ddb"] if gated else None)
+    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"],
+                          info["n_ddb"] if gated else None, info["total_deriv"])
     out["svd_n8192"] = {"value": n / (ms / 1e3), "unit": "singular triplets/s", "ms_per_step": ms,
                         "k_eig_ms": info["ms_eig"],
                         "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -278,8 +278,8 @@ def extras(arrowhead, W, dev, stream, flush, args):
         info.update(arrowhead.herm_arrow_eig(dt, zt, al, opts=opts, info=True,
                                              out={"lam": lam, "U": Uc}, stream=stream)["info"])
     ms = timed_device(f_herm, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval,
-                          info["n_ddb"] if gated else None)
+    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"],
+                          info["n_ddb"] if gated else None, info["total_deriv"])
     out["herm_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                          "k_eig_ms": info["ms_eig"],
                          "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -294,8 +294,8 @@ def extras(arrowhead, W, dev, stream, flush, args):
                                              out={"lam": lam, "X": Q, "Y": Y},
                                              stream=stream)["info"])
     ms = timed_device(f_nsym, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval,
-                          info["n_ddb"] if gated else None)
+    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"],
+                          info["n_ddb"] if gated else None, info["total_deriv"])
     out["nsym_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                          "k_eig_ms": info["ms_eig"],
                          "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -475,9 +475,8 @@ def main():
     value = world * n * args.steps / (total_ms / 1e3)
     info = infos[-1]
     eig_ms = float(np.mean([x["ms_eig"] for x in infos]))
-    per_eval = 6.0 if FORMS[primary][1] == 1 else 3.0
-    flops = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"], per_eval,
-                             info["n_ddb"] if FORMS[primary][2] else None)
+    flops = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"],
+                             info["n_ddb"] if FORMS[primary][2] else None, info["total_deriv"])
     achieved = flops / (eig_ms / 1e3) / 1e12
     # the all-FP64 bisection's algorithmic work (its measured step count) over
     # this form's k_eig time: the rate at which the paper's work gets done
@@ -485,7 +484,7 @@ def main():
     if "fp64" in runs:
         i64 = runs["fp64"][1][-1]
         eq = eig_kernel_flops(n, i64["n_reduced"], i64["total_iter"],
-                              i64["fix_iter"], vectors=True) / (eig_ms / 1e3) / 1e12
+                              i64["fix_iter"]) / (eig_ms / 1e3) / 1e12
     traffic = None
     if (KEIG_TRAFFIC["form"] == primary and KEIG_TRAFFIC["n"] == n
             and KEIG_TRAFFIC["src_sha256"] == csrc_sha256()):

@@ -113,6 +113,9 @@ typedef struct ae_info {
     float ms_vectors;     /* placement and eigenvector columns */
     int n_ddb;            /* with opts->bgate: eigenpairs whose b was recomputed in
                              double-double */
+    long long total_deriv; /* Newton finish: the evaluations of total_iter - fix_iter
+                              (the solves of Algorithm 1's shift) that also formed
+                              the derivative */
 } ae_info;
 
 /* Optional per-eigenpair diagnostics (device arrays of length n, any may be

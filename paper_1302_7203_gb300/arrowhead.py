@@ -59,7 +59,8 @@ class AeInfo(ctypes.Structure):
                 ("max_Kb", ctypes.c_double),
                 ("max_Knu", ctypes.c_double), ("ms_reduce", ctypes.c_float),
                 ("ms_eig", ctypes.c_float), ("ms_fix", ctypes.c_float),
-                ("ms_vectors", ctypes.c_float), ("n_ddb", ctypes.c_int)]
+                ("ms_vectors", ctypes.c_float), ("n_ddb", ctypes.c_int),
+                ("total_deriv", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

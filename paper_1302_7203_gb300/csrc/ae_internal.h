@@ -25,7 +25,8 @@ enum {
     C_DDB = 12,       // b recomputed in double-double under the Algorithm 5 gate
     C_COUNT = 16
 };
-enum { C64_ITERS = 0, C64_MAXKB = 1, C64_MAXKNU = 2, C64_ITERS_FIX = 3, C64_COUNT = 4 };
+enum { C64_ITERS = 0, C64_MAXKB = 1, C64_MAXKNU = 2, C64_ITERS_FIX = 3, C64_DERIV = 4,
+       C64_COUNT = 5 };
 
 // k_check flag bits
 enum { CF_UNSORTED = 1, CF_ZERO = 2, CF_BAD = 4, CF_ZEROPOLE = 8 };

@@ -315,6 +315,7 @@ __device__ __forceinline__ void store_result(const Scratch &S, int k, const EigR
 __device__ __forceinline__ void record_stats(const Scratch &S, const EigResult &r,
                                              bool fix = false) {
     atomicAdd(S.cnt64 + C64_ITERS, (unsigned long long)r.iters);
+    if (r.iters_d && !fix) atomicAdd(S.cnt64 + C64_DERIV, (unsigned long long)r.iters_d);
     if (fix) atomicAdd(S.cnt64 + C64_ITERS_FIX, (unsigned long long)r.iters);
     atomicMax(S.cnt + C_MAXIT, r.iters);
     if (r.flags & AE_FLAG_CAPPED) atomicAdd(S.cnt + C_CAPPED, 1);

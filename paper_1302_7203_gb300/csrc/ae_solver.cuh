@@ -43,8 +43,9 @@ struct EigResult {
     double b;       // element b of the shifted inverse (NaN for DPR1 solves)
     double Kb;      // K_b of Eq. (K2)
     int pole;       // reduced pole index of the shift, -1 if none
-    int iters;      // FP64 bisection steps
+    int iters;      // FP64 evaluations (bisection steps or Newton evaluations)
     int flags;
+    int iters_d;    // of those, Newton evaluations that also formed F' 
 };
 
 // ---------------------------------------------------------------------------
@@ -627,8 +628,9 @@ template <class FD>
 __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, double kappa,
                                              double gl, double gr, bool lv, bool rv,
                                              int max_iter, double &left, double &right,
-                                             bool &fell_back, double dF0 = NAN) {
-    int it = 0;
+                                             bool &fell_back, double dF0 = NAN,
+                                             int *nderiv = nullptr) {
+    int it = 0, itd = 0;
     fell_back = false;
     bool need_d = !isfinite(dF0);
     double dF = need_d ? -1.0 : dF0;
@@ -641,6 +643,7 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
         while (right - left > TWO_EPS * fabs(0.5 * (left + right)) && it < max_iter) {
             const double F = fd(x, need_d, dF, err);
             ++it;
+            itd += need_d ? 1 : 0;
             const bool pos = F > 0.0;
             if (pos) { left = x; lv = true; }
             else { right = x; rv = true; }
@@ -705,6 +708,7 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
             else { left = right; right = gr; lv = rv = true; fell_back = true; }
         }
     }
+    if (nderiv) *nderiv = itd;
     return it;
 }
 
@@ -757,7 +761,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
     auto G = [&](double x) { return (b - x) + c * rcp(x); };
     const bool f32 = o.precision == 1 && R.has_f32();
     double left, right;
-    int it = 0;
+    int it = 0, itd = 0;
     if (newton) {
         // F's poles are 1/delta_j (j != i) and 0; the one nearest the searched
         // side is 1/delta_{i-1} (side > 0, i > 0) or 1/delta_{i+1} (side < 0,
@@ -836,7 +840,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
         }
         bool fb;
         it = newton_finish(FD, side, pole, -1.0, gl, gr, lv, rv, o.max_iter, left, right, fb,
-                           dF0);
+                           dF0, &itd);
         if (fb) res.flags |= 64;
     } else {
         // Gershgorin bracket of Algorithm 3 for the inverse: diagonal {1/delta_j, 0},
@@ -870,6 +874,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
     res.lam = sigma + res.mu;
     res.pole = i;
     res.iters = it;
+    res.iters_d = itd;
     res.flags |= (it >= o.max_iter) ? 16 : 0;
     return res;
 }
@@ -940,7 +945,7 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
     // (no FP32 opening here: with a shift next to lambda, nu ~ 1/(lambda - shift)
     // is far outside what a power-of-two rescaled FP32 copy can represent, and
     // these solves are a few per cent of all eigenpairs)
-    int it = 0;
+    int it = 0, itd = 0;
     if (o.finish == 1) {
         // the Newton finish on dir * phi, which decreases through the zero; the
         // zero lies beyond all poles {1/delta_j, 0} on the side sign(rho), where
@@ -963,7 +968,7 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
         };
         bool fb;
         it = newton_finish(FD, side, pole, 0.0, left, right, true, true, o.max_iter, left, right,
-                           fb);
+                           fb, NAN, &itd);
     } else {
         double mid = 0.5 * (left + right);
         while (right - left > TWO_EPS * fabs(mid) && it < o.max_iter) {
@@ -978,6 +983,7 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
     res.mu = 1.0 / nu;
     res.lam = shift + res.mu;
     res.iters = it;
+    res.iters_d = itd;
     res.flags |= (it >= o.max_iter) ? 16 : 0;
     return res;
 }
