@@ -53,7 +53,8 @@ sys.path.insert(0, ROOT)
 METRIC = "eigenpairs/s at ≤10nε64 rel. err (n=16384, batched); p50/p99 solve latency"
 UNIT = "eigenpairs/s"
 N_DEFAULT = 16384
-LAUNCHES_PER_STEP = 8   # k_check k_rank k_reduce k_eig k_fix_decide k_fix_solve k_place k_vectors
+# k_check k_rank k_reduce k_post k_eig k_fix_decide k_fix_solve k_place k_vectors
+LAUNCHES_PER_STEP = 9
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
 
 
