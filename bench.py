@@ -22,15 +22,14 @@ roofline   the eigenvalue kernel (k_eig): algorithmic FP64 flops per launch
            FP64 ALU peak 152 SMs x 4 flop/clk x 2070 MHz.  Also reported: the
            all-FP64 bisection's algorithmic work over the headline form's k_eig
            time (fp64_bisection_equivalent_tflops).
-forms      fp64_newton_gated (default headline): Algorithm 5 -- b in
-           standard precision unless the spike ratio and K_b ask for
-           double-double -- with the bracketed Newton finish, FP64 throughout.
-           fp64_newton: the same with b always in double-double, the bracketed
-           Newton finish (same Pick function, bracket and stop test as
-           Algorithm 3); fp64: all-FP64 bisection as in Algorithm 3; fp32:
-           FP32 opening bracket then FP64 bisection; fp32_newton and
-           fp32_newton_gated (the Newton forms after an FP32 opening bracket).
-           All six are timed; --form picks the headline.
+forms      fp32_newton_gated (default headline): two FP32 model steps open
+           the search, then the bracketed Newton finish in FP64 (same Pick
+           function, bracket and stop test as Algorithm 3), with Algorithm 5's
+           gates (b in standard precision unless the spike ratio and K_b ask for
+           double-double).  fp64_newton_gated: the same without the FP32
+           opening; fp32_newton / fp64_newton: b always in double-double; fp32:
+           FP32 opening bracket then FP64 bisection; fp64: all-FP64 bisection as
+           in Algorithm 3.  All six are timed; --form picks the headline.
 cpu_baseline  the CPU oracle on a bounded sample of eigenpairs of the same
            matrix, on all host cores.
 --impl reference   times the CPU oracle alone (the reference arm).
@@ -98,12 +97,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--form", default="fp64_newton_gated", choices=list(FORMS),
-                   help="headline form: fp64_newton_gated = Algorithm 5's precision gates "
-                        "with the bracketed Newton finish (default); fp64_newton = the same "
-                        "with b always double-double; fp32 = FP32 opening bracket + FP64 "
-                        "bisection; fp64 = all-FP64 bisection (Algorithm 3); fp32_newton; "
-                        "fp32_newton_gated")
+    p.add_argument("--form", default="fp32_newton_gated", choices=list(FORMS),
+                   help="headline form: fp32_newton_gated = FP32 opening, Algorithm 5's "
+                        "precision gates and the bracketed Newton finish in FP64 (default); "
+                        "fp64_newton_gated = the same without the FP32 opening; fp64_newton / "
+                        "fp32_newton = b always double-double; fp32 = FP32 opening bracket + "
+                        "FP64 bisection; fp64 = all-FP64 bisection (Algorithm 3)")
     p.add_argument("--forms", default=",".join(FORMS),
                    help="comma-separated forms to time beside the headline (default: all)")
     p.add_argument("--no-e2e", action="store_true")

@@ -360,6 +360,23 @@ __device__ __forceinline__ float secular_sum_f32(const P &R, const Team &T, floa
     return T.sumf(acc0 + acc1);
 }
 
+// T(y) and T'(y) = sum_{j != skip} zz_j / (1 - y D_j)^2 together (the FP32
+// model steps that open the Newton finish); same scaled data as above.
+template <class P, class Team>
+__device__ __forceinline__ float2 secular_sum_f32_d(const P &R, const Team &T, float sh,
+                                                    float sl, float sc, int skip, float y) {
+    float a0 = 0.f, d0 = 0.f;
+    for (int j = T.rank; j < R.m; j += Team::size) {
+        if (j == skip) continue;
+        const float D = R.shifted_f32(j, sh, sl) * sc;
+        const float rt = rcp_f32(fmaf(-y, D, 1.f));           // 1 / (1 - y D)
+        const float q = R.z2f(j) * rcp_f32(D) * rt;            // zz / (D (1 - y D))
+        a0 += q;
+        d0 = fmaf(q * D, rt, d0);                              // zz / (1 - y D)^2
+    }
+    return make_float2(T.sumf(a0), T.sumf(d0));
+}
+
 // Algorithm 1, first part: the shift pole i and the side (+1: lambda > p_i).
 template <class P, class Team>
 __device__ __forceinline__ void select_shift(const P &R, const Team &T, int k, int &i,
@@ -629,13 +646,15 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
                                              double gl, double gr, bool lv, bool rv,
                                              int max_iter, double &left, double &right,
                                              bool &fell_back, double dF0 = NAN,
-                                             int *nderiv = nullptr) {
+                                             int *nderiv = nullptr, double x0 = NAN) {
     int it = 0, itd = 0;
     fell_back = false;
     bool need_d = !isfinite(dF0);
     double dF = need_d ? -1.0 : dF0;
     for (;;) {
-        double x = 0.5 * (left + right);
+        // the first trial point: x0 when the caller has one inside the bracket
+        double x = (x0 > left && x0 < right) ? x0 : 0.5 * (left + right);
+        x0 = NAN;
         double pend = NAN;          // last model point from the good side
         double jump = 0.0;
         bool nudged = false, noisy = false, jumping = false, pside = false;
@@ -818,14 +837,38 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
             return (b - x) - c * (S.x - rx);
         };
         const double gl = left, gr = right;
-        bool lv = true, rv = true;
+        const bool lv = true, rv = true;
+        // FP32 opening for the Newton finish: two one-pole model steps on the
+        // rescaled FP32 copy (F and F' with c S(x) = K T(y)) give the first
+        // FP64 trial point; they move no bracket end (unverified)
+        double x0 = NAN;
         if (f32) {
-            double l, r;
-            if (fp32_narrow(R, T, sigma, i, c, +1, G, left, right, l, r)) {
-                lv = !(l > left);
-                rv = !(r < right);
-                left = l;
-                right = r;
+            const double big = fmax(fabs(left), fabs(right));
+            const double s = ldexp(1.0, ilogb(big));
+            const double scd = s / R.f32_scale();
+            float sh = 0.f, sl = 0.f;
+            R.f32_shift(sigma, i, sh, sl);
+            if (big > 0.0 && isfinite(big) && scd > 0x1p-120 && scd < 0x1p120 && isfinite(sh)) {
+                const float sc = (float)scd;
+                const double K = c * s / R.zs;
+                double x = 0.5 * (left + right);
+                for (int t = 0; t < 2; ++t) {
+                    const float y = (float)(x / s);
+                    const double xe = s * (double)y;
+                    const float2 Tf = secular_sum_f32_d(R, T, sh, sl, sc, i, y);
+                    const double rx = rcp(xe);
+                    const double F = (b - xe) + c * rx - K * (double)Tf.x;
+                    const double dF = -1.0 - c * rx * rx - K * (double)Tf.y / s;
+                    const double d0 = fabs(xe - pole);
+                    const double beta = (-1.0 - dF) * d0 * d0;
+                    const double a = F + xe + (side > 0 ? -beta : beta) / d0;
+                    double xs, xb;
+                    quad_roots(a, pole, beta, xs, xb);
+                    const double xn = side > 0 ? xb : xs;
+                    if (!(xn > left && xn < right)) break;
+                    x = xn;
+                }
+                x0 = x;
             } else {
                 res.flags |= 64;
             }
@@ -840,7 +883,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
         }
         bool fb;
         it = newton_finish(FD, side, pole, -1.0, gl, gr, lv, rv, o.max_iter, left, right, fb,
-                           dF0, &itd);
+                           dF0, &itd, x0);
         if (fb) res.flags |= 64;
     } else {
         // Gershgorin bracket of Algorithm 3 for the inverse: diagonal {1/delta_j, 0},
