@@ -841,7 +841,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
         // FP32 opening for the Newton finish: two one-pole model steps on the
         // rescaled FP32 copy (F and F' with c S(x) = K T(y)) give the first
         // FP64 trial point; they move no bracket end (unverified)
-        double x0 = NAN;
+        double x0 = NAN, dF0 = NAN;
         if (f32) {
             const double big = fmax(fabs(left), fabs(right));
             const double s = ldexp(1.0, ilogb(big));
@@ -852,6 +852,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                 const float sc = (float)scd;
                 const double K = c * s / R.zs;
                 double x = 0.5 * (left + right);
+                double dF32 = NAN, step = INFINITY;
                 for (int t = 0; t < 2; ++t) {
                     const float y = (float)(x / s);
                     const double xe = s * (double)y;
@@ -866,16 +867,20 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                     quad_roots(a, pole, beta, xs, xb);
                     const double xn = side > 0 ? xb : xs;
                     if (!(xn > left && xn < right)) break;
+                    step = fabs(xn - x);
+                    dF32 = dF;
                     x = xn;
                 }
                 x0 = x;
+                // an FP32 step that short leaves F' known to FP32 accuracy, which
+                // serves as the first FP64 evaluation's F'
+                if (step < 0x1p-20 * fabs(x0)) dF0 = dF32;
             } else {
                 res.flags |= 64;
             }
         }
         // a bracket this tight means all of F's weight sits at its nearest pole
         // to that accuracy: F'(x) = -1 - W / (x - pole)^2 is the first F'
-        double dF0 = NAN;
         const double xm = 0.5 * (left + right);
         if (right - left < 0x1p-26 * fabs(xm)) {
             const double dx = xm - pole;
