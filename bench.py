@@ -14,7 +14,8 @@ e2e        the same metric through arrow_eig_host: pinned host d, z in, lambda
 roofline   the eigenvalue kernel (k_eig): algorithmic FP64 flops per launch
            (3 per term per evaluation of the secular function: subtract,
            divide, add, as in Algorithm 3; 3 more per Newton evaluation that
-           forms the derivative; 3 per term for the shift choice; 20 per term for the
+           forms the derivative; 3 per term for the shift choice where it ran
+           in FP64; 20 per term for the
            double-double element b, or 3 for a standard-precision b under
            Algorithm 5's gate; 6 per eigenvector component, which k_eig
            writes as soon as each eigenvalue is known) over its event-timed
@@ -26,8 +27,10 @@ forms      fp32_newton_gated (default headline): two FP32 model steps open
            the search, then the bracketed Newton finish in FP64 (same Pick
            function, bracket and stop test as Algorithm 3), with Algorithm 5's
            gates (b in standard precision unless the spike ratio and K_b ask for
-           double-double).  fp64_newton_gated: the same without the FP32
-           opening; fp32_newton / fp64_newton: b always in double-double; fp32:
+           double-double); Algorithm 1's midpoint test in FP32 with an error
+           bound, in FP64 only where the bound leaves its sign open.
+           fp64_newton_gated: the same without FP32 (opening and midpoint
+           test); fp32_newton / fp64_newton: b always in double-double; fp32:
            FP32 opening bracket then FP64 bisection; fp64: all-FP64 bisection as
            in Algorithm 3.  All six are timed; --form picks the headline.
 cpu_baseline  the CPU oracle on a bounded sample of eigenpairs of the same
@@ -165,22 +168,35 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
-def eig_kernel_flops(n, ncomp, total_iter, fix_iter, n_ddb=None, total_deriv=0, vectors=True):
+def eig_kernel_flops(n, ncomp, total_iter, fix_iter, n_ddb=None, total_deriv=0, vectors=True,
+                     n_mid=None):
     """Algorithmic FP64 flops of one k_eig launch (see module docstring).
 
-    Per term: 3 flops for the shift choice (Algorithm 1's midpoint test); 20
-    for the double-double b, or 3 (subtract, divide, add) for a standard one
+    Per term: 3 flops for the shift choice (Algorithm 1's midpoint test) where
+    it ran in FP64 (n_mid = the eigenpairs whose test did; None: all of them);
+    20 for the double-double b, or 3 (subtract, divide, add) for a standard one
     where Algorithm 5's gate kept it (n_ddb = the eigenpairs it sent to
     double-double; None: all double-double); 3 per FP64 evaluation of the
     secular function (subtract, divide, add, as in Algorithm 3) and 3 more per
     Newton evaluation that also formed the derivative (total_deriv).  vectors:
     6 flops per eigenvector component (Eq. Aeigenvec: 2 subtractions and a
-    division; square, add and scale to normalise), which k_eig writes."""
+    division; square, add and scale to normalise), which k_eig writes.  Work
+    done in FP32 (the opening model steps, the certified midpoint tests) is
+    not counted."""
     terms = n - 2                    # each O(n) pass runs over the other poles
     b = 20.0 * ncomp if n_ddb is None else 3.0 * ncomp + 20.0 * n_ddb
     vec = 6.0 * (n - 1) * ncomp if vectors else 0.0
     evals = 3.0 * (total_iter - fix_iter) + 3.0 * total_deriv
-    return terms * (evals + 3.0 * ncomp + b) + vec
+    mid = 3.0 * (ncomp if n_mid is None else n_mid)
+    return terms * (evals + mid + b) + vec
+
+
+def form_flops(n, info, form):
+    """eig_kernel_flops for a run of `form` from its ae_info counters."""
+    prec, _, gate = FORMS[form]
+    return eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"],
+                            info["n_ddb"] if gate else None, info["total_deriv"],
+                            n_mid=info["n_mid64"] if prec == 1 else None)
 
 
 def cpu_baseline(d, z, alpha, n, seconds):
@@ -249,9 +265,7 @@ def extras(arrowhead, W, dev, stream, flush, args):
         info.update(arrowhead.dpr1_eig(dt, ut, rho, opts=opts, info=True,
                                        out={"lam": lam, "Q": Q}, stream=stream)["info"])
     ms = timed_device(f_dpr1, 3, 1, stream, flush)
-    gated = FORMS[args.form][2] == 1
-    fl = eig_kernel_flops(n + 1, info["n_reduced"], info["total_iter"], info["fix_iter"],
-                          info["n_ddb"] if gated else None, info["total_deriv"])
+    fl = form_flops(n + 1, info, args.form)
     out["dpr1_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                          "k_eig_ms": info["ms_eig"],
                          "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -263,8 +277,7 @@ def extras(arrowhead, W, dev, stream, flush, args):
         info.update(arrowhead.tri_arrow_svd(dt, zt, al, opts=opts, info=True,
                                             out={"s": lam, "U": U, "V": Q}, stream=stream)["info"])
     ms = timed_device(f_svd, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"],
-                          info["n_ddb"] if gated else None, info["total_deriv"])
+    fl = form_flops(n, info, args.form)
     out["svd_n8192"] = {"value": n / (ms / 1e3), "unit": "singular triplets/s", "ms_per_step": ms,
                         "k_eig_ms": info["ms_eig"],
                         "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -278,8 +291,7 @@ def extras(arrowhead, W, dev, stream, flush, args):
         info.update(arrowhead.herm_arrow_eig(dt, zt, al, opts=opts, info=True,
                                              out={"lam": lam, "U": Uc}, stream=stream)["info"])
     ms = timed_device(f_herm, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"],
-                          info["n_ddb"] if gated else None, info["total_deriv"])
+    fl = form_flops(n, info, args.form)
     out["herm_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                          "k_eig_ms": info["ms_eig"],
                          "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -294,8 +306,7 @@ def extras(arrowhead, W, dev, stream, flush, args):
                                              out={"lam": lam, "X": Q, "Y": Y},
                                              stream=stream)["info"])
     ms = timed_device(f_nsym, 3, 1, stream, flush)
-    fl = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"],
-                          info["n_ddb"] if gated else None, info["total_deriv"])
+    fl = form_flops(n, info, args.form)
     out["nsym_n8192"] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                          "k_eig_ms": info["ms_eig"],
                          "frac_fp64": fl / (info["ms_eig"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
@@ -475,8 +486,7 @@ def main():
     value = world * n * args.steps / (total_ms / 1e3)
     info = infos[-1]
     eig_ms = float(np.mean([x["ms_eig"] for x in infos]))
-    flops = eig_kernel_flops(n, info["n_reduced"], info["total_iter"], info["fix_iter"],
-                             info["n_ddb"] if FORMS[primary][2] else None, info["total_deriv"])
+    flops = form_flops(n, info, primary)
     achieved = flops / (eig_ms / 1e3) / 1e12
     # the all-FP64 bisection's algorithmic work (its measured step count) over
     # this form's k_eig time: the rate at which the paper's work gets done

@@ -68,6 +68,8 @@ extern "C" {
 #define AE_FLAG_SINGULAR 32   /* remedy found a zero denominator: lambda = sigma */
 #define AE_FLAG_FP32_FALLBACK 64 /* FP32 bracket failed its FP64 check */
 #define AE_FLAG_DDB 128       /* with opts->bgate: b recomputed in double-double */
+#define AE_FLAG_MID64 256     /* with AE_FP32_BRACKET: Algorithm 1's midpoint test was
+                                 not settled by its FP32 evaluation and ran in FP64 */
 
 typedef struct ae_opts {
     int precision;     /* AE_FP64 (default) or AE_FP32_BRACKET */
@@ -116,6 +118,8 @@ typedef struct ae_info {
     long long total_deriv; /* Newton finish: the evaluations of total_iter - fix_iter
                               (the solves of Algorithm 1's shift) that also formed
                               the derivative */
+    int n_mid64;          /* with AE_FP32_BRACKET: midpoint tests (Algorithm 1) that
+                             needed their FP64 pass (flag AE_FLAG_MID64) */
 } ae_info;
 
 /* Optional per-eigenpair diagnostics (device arrays of length n, any may be

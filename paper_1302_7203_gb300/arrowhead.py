@@ -28,6 +28,7 @@ AE_FINISH_BISECT = 0
 AE_FINISH_NEWTON = 1
 FLAG_DEFLATED, FLAG_NEARZERO, FLAG_OTHERPOLE, FLAG_DPR1SHIFT = 1, 2, 4, 8
 FLAG_CAPPED, FLAG_SINGULAR, FLAG_FP32_FALLBACK, FLAG_DDB = 16, 32, 64, 128
+FLAG_MID64 = 256
 
 # every symbol include/arrowhead.h declares
 EXPORTED = ["ae_default_opts", "ae_status_string", "ae_last_cuda_error", "arrow_eig",
@@ -60,7 +61,7 @@ class AeInfo(ctypes.Structure):
                 ("max_Knu", ctypes.c_double), ("ms_reduce", ctypes.c_float),
                 ("ms_eig", ctypes.c_float), ("ms_fix", ctypes.c_float),
                 ("ms_vectors", ctypes.c_float), ("n_ddb", ctypes.c_int),
-                ("total_deriv", ctypes.c_longlong)]
+                ("total_deriv", ctypes.c_longlong), ("n_mid64", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -168,6 +168,7 @@ static int solve_common(ae::Kind kind, int n, const double *d, const double *z, 
             info->max_Kb = bits_to_double(c64[ae::C64_MAXKB]);
             info->max_Knu = bits_to_double(c64[ae::C64_MAXKNU]);
             info->n_ddb = cnt[ae::C_DDB];
+            info->n_mid64 = cnt[ae::C_MID64];
             info->total_deriv = (long long)c64[ae::C64_DERIV];
             if (prof.on) {
                 cudaEventElapsedTime(&info->ms_reduce, prof.ev[0], prof.ev[1]);

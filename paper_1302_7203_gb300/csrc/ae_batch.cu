@@ -552,6 +552,7 @@ static cudaError_t plan_info(const Plan &P, ae_info *info, cudaStream_t st) {
         info->n_capped += c[C_CAPPED];
         info->n_fp32_fallback += c[C_FP32FB];
         info->n_ddb += c[C_DDB];
+        info->n_mid64 += c[C_MID64];
         info->total_deriv += (long long)u[C64_DERIV];
         if (c[C_MAXIT] > info->max_iter_used) info->max_iter_used = c[C_MAXIT];
         info->total_iter += (long long)u[C64_ITERS];

@@ -23,6 +23,7 @@ enum {
     C_MAXIT = 10,
     C_FP32FB = 11,
     C_DDB = 12,       // b recomputed in double-double under the Algorithm 5 gate
+    C_MID64 = 13,     // FP32 midpoint tests that needed the FP64 pass
     C_COUNT = 16
 };
 enum { C64_ITERS = 0, C64_MAXKB = 1, C64_MAXKNU = 2, C64_ITERS_FIX = 3, C64_DERIV = 4,

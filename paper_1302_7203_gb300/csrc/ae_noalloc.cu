@@ -114,6 +114,7 @@ extern "C" int arrow_eig_noalloc(int n, const double *d, const double *z, double
     memcpy(&info->max_Kb, &c64[ae::C64_MAXKB], sizeof(double));
     memcpy(&info->max_Knu, &c64[ae::C64_MAXKNU], sizeof(double));
     info->n_ddb = cnt[ae::C_DDB];
+    info->n_mid64 = cnt[ae::C_MID64];
     info->total_deriv = (long long)c64[ae::C64_DERIV];
     if (cnt[ae::C_FLAGS] & ae::CF_BAD) return AE_ERR_INPUT;
     if (cnt[ae::C_CAPPED]) return AE_ERR_NOCONV;

@@ -321,6 +321,7 @@ __device__ __forceinline__ void record_stats(const Scratch &S, const EigResult &
     if (r.flags & AE_FLAG_CAPPED) atomicAdd(S.cnt + C_CAPPED, 1);
     if (r.flags & AE_FLAG_FP32_FALLBACK) atomicAdd(S.cnt + C_FP32FB, 1);
     if (r.flags & AE_FLAG_DDB) atomicAdd(S.cnt + C_DDB, 1);
+    if (r.flags & AE_FLAG_MID64) atomicAdd(S.cnt + C_MID64, 1);
     if (isfinite(r.Kb)) atomic_max_nonneg(S.cnt64 + C64_MAXKB, r.Kb);
 }
 
@@ -337,8 +338,9 @@ __device__ __forceinline__ void eig_item(const typename PolesOf<K>::type &R, con
         res = {a, S.prm[P_ALPHA_LO], a, NAN, 0.0, -1, 0, 0};
     } else {
         int i, side;
-        select_shift(R, T, k, i, side);
+        const bool mid64 = select_shift(R, T, k, i, side, o.precision == 1);
         res = solve_shifted(R, T, i, side, o, buf);
+        if (mid64) res.flags |= AE_FLAG_MID64;
     }
     if (T.rank == 0) {
         store_result(S, k, res);

@@ -162,6 +162,13 @@ struct ArrowPoles {
     __device__ __forceinline__ float shifted_f32(int j, float sh, float sl) const {
         return (__ldg(pdh + j) - sh) + (__ldg(pdl + j) - sl);
     }
+    // the same, and a magnitude g with |error| <= 2 u |result| + 2^-45 g + 2^-147
+    // (u = 2^-24; the hi + lo splits are exact to 2^-48 relative)
+    __device__ __forceinline__ float shifted_f32_mag(int j, float sh, float sl, float &g) const {
+        const float h = __ldg(pdh + j);
+        g = fabsf(h) + fabsf(sh);
+        return (h - sh) + (__ldg(pdl + j) - sl);
+    }
     __device__ __forceinline__ double f32_scale() const { return ds; }
     __device__ __forceinline__ float z2f(int j) const { return __ldg(pz2f + j); }
     __device__ __forceinline__ bool has_f32() const { return pdh != nullptr; }
@@ -222,6 +229,13 @@ struct TsvdPoles {
     __device__ __forceinline__ float shifted_f32(int j, float sh, float sl) const {
         const float h = __ldg(pdh + j), l = __ldg(pdl + j);
         return ((h - sh) + (l - sl)) * ((h + sh) + (l + sl));
+    }
+    // with g = (d_j + d_i)^2 (scaled): |error| <= 6 u |result| + 2^-44 g + 2^-145
+    __device__ __forceinline__ float shifted_f32_mag(int j, float sh, float sl, float &g) const {
+        const float h = __ldg(pdh + j), l = __ldg(pdl + j);
+        const float s = (h + sh) + (l + sl);
+        g = s * s;
+        return ((h - sh) + (l - sl)) * s;
     }
     __device__ __forceinline__ double f32_scale() const { return ds * ds; }
     __device__ __forceinline__ float z2f(int j) const { return __ldg(pz2f + j); }
@@ -378,25 +392,85 @@ __device__ __forceinline__ float2 secular_sum_f32_d(const P &R, const Team &T, f
 }
 
 // Algorithm 1, first part: the shift pole i and the side (+1: lambda > p_i).
+// The test is the sign of F at the midpoint x = p_k + middle of lambda's
+// interval, F(x) = (alpha - p_k - middle) - sum_j zeta_j^2 / ((p_j - p_k) - middle).
+// With f32 set it is first evaluated in FP32 on the scaled copies, with a
+// bound on its error; when that bound, plus a bound on the error of the FP64
+// evaluation, leaves the sign in no doubt, the FP64 sign is known and its pass
+// is skipped, so the chosen shift is the one the FP64 test gives.  Returns true
+// when the FP64 pass ran in that mode.
+//
+// The bound.  Every pole lies at least |middle| from x (the nearest two sit at
+// +-middle), so |p_j - p_k| <= 2 |D_j| with D_j = (p_j - p_k) - middle.  In FP32
+// (unit u = 2^-24) the scaled D_j is computed with error below
+// 14 u |D_j| + 2^-44 g_j + 2^-145 (shifted_f32_mag, doubled by the factor 2,
+// plus the roundings of middle and of the subtraction), so below 16 u |D_j|
+// once |D_j| >= 2^-20 g_j + 2^-100 (else the FP64 pass runs).  The approximate
+// reciprocal (one ulp) and the spike and product roundings bring each term to
+// 20 u |t_j|, plus 2^-150 (|r_j| + 1) where they are subnormal.  Summation over
+// L terms per thread and a butterfly adds (L + 4) u sum |t_j| (a CTA team sums
+// its warps' FP32 partials in double).  So |T - T_exact| <= (L + 24) u A' +
+// 2^-150 (B + m), with A' = sum |t_j| below 2 A and B below 2 B' (A, B' the FP32
+// sums of |t_j| and |r_j|).  The FP64 pass errs by at most (L + 16) 2^-52 A64 on
+// the same scale, far below the slack the margin keeps for it.
 template <class P, class Team>
-__device__ __forceinline__ void select_shift(const P &R, const Team &T, int k, int &i,
-                                             int &side) {
+__device__ __forceinline__ bool select_shift(const P &R, const Team &T, int k, int &i,
+                                             int &side, bool f32 = false) {
     const int m = R.m;
     if (k == 0) {
         i = 0; side = +1;
-    } else if (k == m) {
+        return false;
+    }
+    if (k == m) {
         i = m - 1; side = -1;
-    } else {
-        const double sk = R.pole(k);
-        const double middle = 0.5 * R.shifted(k - 1, sk, k);
-        const dd a = R.a_dd(sk, k);
+        return false;
+    }
+    const double sk = R.pole(k);
+    const double middle = 0.5 * R.shifted(k - 1, sk, k);
+    const dd a = R.a_dd(sk, k);
+    const double am = a.hi - middle;
+    const double L = (double)((m + Team::size - 1) / Team::size);
+    int sgn = 0;
+    if (f32 && R.has_f32() && L < 0x1p16) {
+        float sh, sl;
+        R.f32_shift(sk, k, sh, sl);
+        const double sc = R.f32_scale();
+        const float mf = (float)(middle * sc);
+        float tf = 0.f, af = 0.f, bf = 0.f;
+        bool bad = false;
+        for (int j = T.rank; j < m; j += Team::size) {
+            float g;
+            const float D = R.shifted_f32_mag(j, sh, sl, g) - mf;
+            bad |= !(fabsf(D) >= fmaf(g, 0x1p-20f, 0x1p-100f));
+            const float r = rcp_f32(D);
+            const float t = R.z2f(j) * r;
+            tf += t;
+            af += fabsf(t);
+            bf += fabsf(r);
+        }
+        if (bad) bf = INFINITY;
+        tf = T.sumf(tf);
+        af = T.sumf(af);
+        bf = T.sumf(bf);
+        // S = (sc / zs) T with the power-of-two scalings of the copies
+        const double f = sc / R.zs;
+        const double F32 = am - f * (double)tf;
+        const double ET = 2.0 * (L + 24.0) * 0x1p-24 * (2.0 * (double)af) +
+                          0x1p-148 * ((double)bf + (double)m);   // doubled again
+        const double M = f * ET * (1.0 + 0x1p-20) + (L + 16.0) * 0x1p-52 * fabs(am);
+        if (isfinite(F32) && fabs(F32) > M * (1.0 + 0x1p-40)) sgn = F32 > 0.0 ? 1 : -1;
+    }
+    const bool ran64 = sgn == 0;
+    if (ran64) {
         double acc = 0.0;
         for (int j = T.rank; j < m; j += Team::size)
             acc = fma(R.z2(j), rcp(R.shifted(j, sk, k) - middle), acc);
-        const double F = (a.hi - middle) - T.sum(acc);
-        if (F < 0.0) { i = k; side = +1; }
-        else { i = k - 1; side = -1; }
+        const double F = am - T.sum(acc);
+        sgn = F < 0.0 ? -1 : 1;
     }
+    if (sgn < 0) { i = k; side = +1; }
+    else { i = k - 1; side = -1; }
+    return f32 && ran64;
 }
 
 // T(shift, skip) = -(alpha - shift) + sum_{j != skip} zeta_j^2 / (p_j - shift) in
