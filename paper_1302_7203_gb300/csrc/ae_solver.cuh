@@ -248,6 +248,30 @@ __device__ __forceinline__ float rcp_f32(float x) {
     return r;
 }
 
+// v 2^k as an unevaluated float pair hi + lo with |v 2^k - hi - lo| <= 2^-46 |v 2^k|,
+// formed by integer operations on v's bits (no FP64 instruction): hi takes the
+// top 24 bits of the significand (truncated), lo the next 23.  A scaled
+// exponent below -100 gives 0, one above 100 gives +-2^100 (callers use this
+// only where such terms are negligible).
+__device__ __forceinline__ void split_df(double v, int k, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+    const unsigned sgn = bh & 0x80000000u;
+    const int e = (int)((bh >> 20) & 0x7ffu) - 1023 + k;
+    if (e < -100) {
+        hi = 0.f;
+        lo = 0.f;
+    } else if (e > 100) {
+        hi = __uint_as_float(sgn | (227u << 23));
+        lo = 0.f;
+    } else {
+        hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((bh & 0xfffffu) << 3) |
+                             (bl >> 29));
+        const unsigned eb = sgn | ((unsigned)(e + 104) << 23);   // 2^(e - 23)
+        lo = __uint_as_float(eb | ((bl >> 6) & 0x7fffffu)) - __uint_as_float(eb);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // O(n) passes
 // ---------------------------------------------------------------------------
@@ -326,6 +350,60 @@ __device__ __forceinline__ double2 secular_sum_d_stored(const double2 *buf, int 
         d0 = fma(qa, a.x * ra, d0);
     }
     return make_double2(T.sum(s0 + s1), T.sum(d0 + d1));
+}
+
+// S(x) in double-float and S'(x) in compensated FP32 from the stored pairs:
+// the trial point that opens the Newton finish (no FP64 instruction per
+// term).  Scaled so that x 2^-kx lies in [1, 2) (delta_j 2^kx, leaving
+// x delta_j unchanged) and c_j 2^-kc <= 2.  Each term: t = 1 - x delta_j
+// (exact product and TwoSum), r = 1/t (FP32 seed and one correction), q = c_j r
+// (relative error ~2^-44), added to a Neumaier sum; S' adds q (delta_j r), all
+// of one sign, with Kahan compensation (relative error below 2^-20).  Terms
+// whose scaled delta_j or c_j falls outside 2^+-100 contribute below
+// 2^-100 of the largest.  Returns (S, S') unscaled; `ok` is false when a
+// result is not finite or S is too small for those bounds.
+template <class Team>
+__device__ __forceinline__ double2 secular_sum_df_stored(const double2 *buf, int m,
+                                                         const Team &T, double x, int kx,
+                                                         int kc, bool &ok) {
+    const double xs = ldexp(x, -kx);
+    const float xh = (float)xs;
+    const float xl = (float)(xs - (double)xh);
+    float sh = 0.f, sl = 0.f, dh = 0.f, dc = 0.f;
+    for (int j = T.rank; j < m; j += Team::size) {
+        const double2 a = buf[j];
+        float Dh, Dl, ch, cl;
+        split_df(a.x, kx, Dh, Dl);
+        split_df(a.y, -kc, ch, cl);
+        // t = 1 - x D = (1 - ph) - pl, ph + pl = x D
+        const float ph = xh * Dh;
+        const float pl = fmaf(xh, Dl, fmaf(xl, Dh, fmaf(xh, Dh, -ph)));
+        const float s1 = 1.f - ph;
+        const float bb = s1 - 1.f;
+        const float th = s1;
+        const float tl = ((1.f - (s1 - bb)) + (-ph - bb)) - pl;
+        // r = 1/t
+        const float r0 = rcp_f32(th);
+        const float e = fmaf(-tl, r0, fmaf(-th, r0, 1.f));
+        const float rh = fmaf(r0, e, r0);
+        const float rl = fmaf(r0, e, r0 - rh);
+        // q = c r
+        const float qh = ch * rh;
+        const float ql = fmaf(ch, rl, fmaf(cl, rh, fmaf(ch, rh, -qh)));
+        // S += q (Neumaier)
+        const float u = sh + qh;
+        sl += (fabsf(sh) >= fabsf(qh) ? (sh - u) + qh : (qh - u) + sh) + ql;
+        sh = u;
+        // S' += q D r (Kahan)
+        const float y = fmaf(qh, Dh * rh, -dc);
+        const float w = dh + y;
+        dc = (w - dh) - y;
+        dh = w;
+    }
+    const double S = T.sum((double)sh + (double)sl);
+    const double Sd = T.sum((double)dh - (double)dc);
+    ok = isfinite(S) && isfinite(Sd) && fabs(S) >= 0x1p-60;
+    return make_double2(ldexp(S, kc), ldexp(Sd, kc - kx));
 }
 
 // The same pair from the poles (no stored buffer): with r_j = 1/(delta_j t_j),
@@ -715,16 +793,37 @@ __device__ bool fp32_verify(int dir, F64 f64, double l, double r, double &left, 
 // length is below 2^-26 |x|.  dF0 (finite): an estimate of F' at the start that
 // is that good already (the caller's bracket is that tight), so the first
 // evaluation skips F' too.
+//
+// Local expansion (ca = c finite, the Pick function of the shifted inverse):
+// with q_j = c_j / (1 - x delta_j) all of one sign, S(x + h) = S(x) + h S'(x) +
+// sum_j q_j e_j^2 / (1 - e_j), e_j = h delta_j / (1 - x delta_j), |e_j| <= |h| / rho
+// where rho = |x - pole| is the distance to F's nearest pole other than 0.  So
+//     F(x + h) = F(x) + h F'(x) + c h^2 / (x^2 (x + h))          (1/x term exact)
+// up to c |S| (h/rho)^2 (1 + ...) from the remainder and |h| |c dS'| from an
+// error dS' in S'.  For |h| <= Ha = min(2^-27 rho, err / (4 drel |c S'|)), drel
+// a bound on the relative error of the S' in hand, both stay below a quarter
+// of the rounding bound err of the FP64 evaluation at x, so the expansion is
+// an evaluation of F with the same O(eps) error per term.  After each FP64
+// evaluation the loop keeps that expansion (the anchor) and evaluates trial
+// points within Ha of it from it, at scalar cost; those are not counted as
+// FP64 evaluations.  The S' in hand is the one formed at xs (the last FP64
+// evaluation with F', or dF0's point xdF0 with relative error rel0), moved to
+// x with relative error at most 4 |x - xs| / rho while |x - xs| <= rho / 8.
 template <class FD>
 __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, double kappa,
                                              double gl, double gr, bool lv, bool rv,
                                              int max_iter, double &left, double &right,
                                              bool &fell_back, double dF0 = NAN,
-                                             int *nderiv = nullptr, double x0 = NAN) {
-    int it = 0, itd = 0;
+                                             int *nderiv = nullptr, double x0 = NAN,
+                                             double ca = NAN, double xdF0 = NAN,
+                                             double rel0 = INFINITY) {
+    int it = 0, itd = 0, itl = 0;
     fell_back = false;
     bool need_d = !isfinite(dF0);
     double dF = need_d ? -1.0 : dF0;
+    double xsrc = xdF0, rsrc = need_d ? INFINITY : rel0;
+    double cSs = need_d ? 0.0 : -1.0 - dF0 - ca / xdF0 / xdF0;   // c S' at xsrc
+    double xa = NAN, Fa = 0.0, dFa = 0.0, Ha = -1.0;
     for (;;) {
         // the first trial point: x0 when the caller has one inside the bracket
         double x = (x0 > left && x0 < right) ? x0 : 0.5 * (left + right);
@@ -734,9 +833,37 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
         bool nudged = false, noisy = false, jumping = false, pside = false;
         double err = 0.0;
         while (right - left > TWO_EPS * fabs(0.5 * (left + right)) && it < max_iter) {
-            const double F = fd(x, need_d, dF, err);
-            ++it;
-            itd += need_d ? 1 : 0;
+            double F;
+            if (fabs(x - xa) <= Ha && itl < 64) {
+                const double h = x - xa;
+                F = Fa + h * (dFa + (ca / xa) * (h / xa) / x);   // (no overflow)
+                dF = dFa;
+                ++itl;
+            } else {
+                F = fd(x, need_d, dF, err);
+                ++it;
+                itd += need_d ? 1 : 0;
+                if (need_d) {
+                    xsrc = x;
+                    rsrc = 0x1p-40;
+                    cSs = -1.0 - dF - ca / x / x;
+                }
+                Ha = -1.0;
+                if (isfinite(ca) && isfinite(rsrc)) {
+                    const double rho = fabs(x - pole);
+                    const double dist = fabs(x - xsrc);
+                    const double drel = rsrc + 4.0 * dist / rho;
+                    double H = 0x1p-27 * rho;
+                    if (fabs(cSs) > 0.0) H = fmin(H, 0.25 * err / (drel * fabs(cSs)));
+                    if (dist <= 0.125 * rho && H > 0.0) {
+                        xa = x;
+                        Fa = F;
+                        dFa = -1.0 - cSs - ca / x / x;
+                        dF = dFa;
+                        Ha = H;
+                    }
+                }
+            }
             const bool pos = F > 0.0;
             if (pos) { left = x; lv = true; }
             else { right = x; rv = true; }
@@ -960,9 +1087,38 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
             const double dx = xm - pole;
             dF0 = -1.0 - c * (A.usq + 1.0) / (dx * dx);
         }
+        // one more model step from the FP32 point with S in double-float and
+        // S' in compensated FP32 on the stored pairs: the first FP64 trial
+        // point lands within ~2^-40 relative of the zero, where the local
+        // expansion of that one FP64 evaluation closes the bracket; its S'
+        // (relative error below 2^-18 here) seeds the expansion
+        double xdF0 = NAN, rel0 = INFINITY;
+        if (f32 && buf && x0 > left && x0 < right && x0 != 0.0) {
+            bool ok;
+            const int kx = ilogb(x0);
+            const int kc = ilogb(fmax(A.P.hi, A.Q.hi));
+            const double2 Sd = secular_sum_df_stored(buf, R.m, T, x0, kx, kc, ok);
+            if (ok) {
+                const double rx = rcp(x0);
+                const double F = (b - x0) - c * (Sd.x - rx);
+                const double dF = -1.0 - c * fma(rx, rx, Sd.y);
+                const double d0 = fabs(x0 - pole);
+                const double beta = (-1.0 - dF) * d0 * d0;
+                const double a = F + x0 + (side > 0 ? -beta : beta) / d0;
+                double xs, xb;
+                quad_roots(a, pole, beta, xs, xb);
+                const double xn = side > 0 ? xb : xs;
+                if (xn > left && xn < right && fabs(xn - x0) <= 0x1p-8 * d0) {
+                    xdF0 = x0;
+                    dF0 = dF;
+                    rel0 = 0x1p-18;
+                    x0 = xn;
+                }
+            }
+        }
         bool fb;
         it = newton_finish(FD, side, pole, -1.0, gl, gr, lv, rv, o.max_iter, left, right, fb,
-                           dF0, &itd, x0);
+                           dF0, &itd, x0, c, xdF0, rel0);
         if (fb) res.flags |= 64;
     } else {
         // Gershgorin bracket of Algorithm 3 for the inverse: diagonal {1/delta_j, 0},
