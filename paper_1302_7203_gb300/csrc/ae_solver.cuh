@@ -362,6 +362,38 @@ __device__ __forceinline__ double2 secular_sum_d_stored(const double2 *buf, int 
 // whose scaled delta_j or c_j falls outside 2^+-100 contribute below
 // 2^-100 of the largest.  Returns (S, S') unscaled; `ok` is false when a
 // result is not finite or S is too small for those bounds.
+// one term of secular_sum_df_stored, added to (sh + sl) and (dh - dc)
+__device__ __forceinline__ void df_term(double2 a, float xh, float xl, int kx, int kc, float &sh,
+                                        float &sl, float &dh, float &dc) {
+    float Dh, Dl, ch, cl;
+    split_df(a.x, kx, Dh, Dl);
+    split_df(a.y, -kc, ch, cl);
+    // t = 1 - x D = (1 - ph) - pl, ph + pl = x D
+    const float ph = xh * Dh;
+    const float pl = fmaf(xh, Dl, fmaf(xl, Dh, fmaf(xh, Dh, -ph)));
+    const float s1 = 1.f - ph;
+    const float bb = s1 - 1.f;
+    const float th = s1;
+    const float tl = ((1.f - (s1 - bb)) + (-ph - bb)) - pl;
+    // r = 1/t
+    const float r0 = rcp_f32(th);
+    const float e = fmaf(-tl, r0, fmaf(-th, r0, 1.f));
+    const float rh = fmaf(r0, e, r0);
+    const float rl = fmaf(r0, e, r0 - rh);
+    // q = c r
+    const float qh = ch * rh;
+    const float ql = fmaf(ch, rl, fmaf(cl, rh, fmaf(ch, rh, -qh)));
+    // S += q (Neumaier)
+    const float u = sh + qh;
+    sl += (fabsf(sh) >= fabsf(qh) ? (sh - u) + qh : (qh - u) + sh) + ql;
+    sh = u;
+    // S' += q D r (Kahan)
+    const float y = fmaf(qh, Dh * rh, -dc);
+    const float w = dh + y;
+    dc = (w - dh) - y;
+    dh = w;
+}
+
 template <class Team>
 __device__ __forceinline__ double2 secular_sum_df_stored(const double2 *buf, int m,
                                                          const Team &T, double x, int kx,
@@ -369,39 +401,18 @@ __device__ __forceinline__ double2 secular_sum_df_stored(const double2 *buf, int
     const double xs = ldexp(x, -kx);
     const float xh = (float)xs;
     const float xl = (float)(xs - (double)xh);
-    float sh = 0.f, sl = 0.f, dh = 0.f, dc = 0.f;
-    for (int j = T.rank; j < m; j += Team::size) {
+    float sh0 = 0.f, sl0 = 0.f, dh0 = 0.f, dc0 = 0.f;
+    float sh1 = 0.f, sl1 = 0.f, dh1 = 0.f, dc1 = 0.f;
+    int j = T.rank;
+    for (; j + Team::size < m; j += 2 * Team::size) {
         const double2 a = buf[j];
-        float Dh, Dl, ch, cl;
-        split_df(a.x, kx, Dh, Dl);
-        split_df(a.y, -kc, ch, cl);
-        // t = 1 - x D = (1 - ph) - pl, ph + pl = x D
-        const float ph = xh * Dh;
-        const float pl = fmaf(xh, Dl, fmaf(xl, Dh, fmaf(xh, Dh, -ph)));
-        const float s1 = 1.f - ph;
-        const float bb = s1 - 1.f;
-        const float th = s1;
-        const float tl = ((1.f - (s1 - bb)) + (-ph - bb)) - pl;
-        // r = 1/t
-        const float r0 = rcp_f32(th);
-        const float e = fmaf(-tl, r0, fmaf(-th, r0, 1.f));
-        const float rh = fmaf(r0, e, r0);
-        const float rl = fmaf(r0, e, r0 - rh);
-        // q = c r
-        const float qh = ch * rh;
-        const float ql = fmaf(ch, rl, fmaf(cl, rh, fmaf(ch, rh, -qh)));
-        // S += q (Neumaier)
-        const float u = sh + qh;
-        sl += (fabsf(sh) >= fabsf(qh) ? (sh - u) + qh : (qh - u) + sh) + ql;
-        sh = u;
-        // S' += q D r (Kahan)
-        const float y = fmaf(qh, Dh * rh, -dc);
-        const float w = dh + y;
-        dc = (w - dh) - y;
-        dh = w;
+        const double2 b = buf[j + Team::size];
+        df_term(a, xh, xl, kx, kc, sh0, sl0, dh0, dc0);
+        df_term(b, xh, xl, kx, kc, sh1, sl1, dh1, dc1);
     }
-    const double S = T.sum((double)sh + (double)sl);
-    const double Sd = T.sum((double)dh - (double)dc);
+    if (j < m) df_term(buf[j], xh, xl, kx, kc, sh0, sl0, dh0, dc0);
+    const double S = T.sum(((double)sh0 + (double)sl0) + ((double)sh1 + (double)sl1));
+    const double Sd = T.sum(((double)dh0 - (double)dc0) + ((double)dh1 - (double)dc1));
     ok = isfinite(S) && isfinite(Sd) && fabs(S) >= 0x1p-60;
     return make_double2(ldexp(S, kc), ldexp(Sd, kc - kx));
 }
