@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(1024) k_post(int n1, const double *__restrict_
 // (pass 1 staged in its stored-pair slice, which the solve no longer needs), at
 // the position k + #(deflated values >= lambda_k) that the placement gives.
 template <Kind K, Kind VK>
-__global__ void __launch_bounds__(256) k_eig(Scratch S, SolveOpts o, VecArgs va) {
+__global__ void __launch_bounds__(256, 3) k_eig(Scratch S, SolveOpts o, VecArgs va) {
     const int lane = threadIdx.x & 31;
     const int m = S.cnt[C_M];
     const int ncomp = m + 1;
