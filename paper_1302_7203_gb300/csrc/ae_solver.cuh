@@ -805,16 +805,20 @@ __device__ bool fp32_verify(int dir, F64 f64, double l, double r, double &left, 
 // is that good already (the caller's bracket is that tight), so the first
 // evaluation skips F' too.
 //
-// Local expansion (ca = c finite, the Pick function of the shifted inverse):
-// with q_j = c_j / (1 - x delta_j) all of one sign, S(x + h) = S(x) + h S'(x) +
-// sum_j q_j e_j^2 / (1 - e_j), e_j = h delta_j / (1 - x delta_j), |e_j| <= |h| / rho
-// where rho = |x - pole| is the distance to F's nearest pole other than 0.  So
-//     F(x + h) = F(x) + h F'(x) + c h^2 / (x^2 (x + h))          (1/x term exact)
-// up to c |S| (h/rho)^2 (1 + ...) from the remainder and |h| |c dS'| from an
-// error dS' in S'.  For |h| <= Ha = min(2^-27 rho, err / (4 drel |c S'|)), drel
+// Local expansion (ca finite).  Both functions searched here have the form
+// F(x) = kappa x + const + K (S(x) - 1/x) with the terms q_j = c_j / (1 - x delta_j)
+// of S all of one sign beyond the poles (the shifted inverse's Pick function:
+// kappa = -1, K = -c; the DPR1 function: kappa = 0, K = sign * rho); ca = -K.
+// S(x + h) = S(x) + h S'(x) + sum_j q_j e_j^2 / (1 - e_j), e_j = h delta_j /
+// (1 - x delta_j), |e_j| <= |h| / rho where rho = |x - pole| is the distance to
+// F's nearest pole other than 0.  So
+//     F(x + h) = F(x) + h F'(x) + ca h^2 / (x^2 (x + h))          (1/x term exact)
+// up to |K S| (h/rho)^2 (1 + ...) from the remainder and |h| |K dS'| from an
+// error dS' in S'.  For |h| <= Ha = min(2^-27 rho, err / (4 drel |K S'|)), drel
 // a bound on the relative error of the S' in hand, both stay below a quarter
-// of the rounding bound err of the FP64 evaluation at x, so the expansion is
-// an evaluation of F with the same O(eps) error per term.  After each FP64
+// of the rounding bound err of the FP64 evaluation at x (which includes
+// 2^-52 |K S|), so the expansion is an evaluation of F with the same O(eps)
+// error per term.  After each FP64
 // evaluation the loop keeps that expansion (the anchor) and evaluates trial
 // points within Ha of it from it, at scalar cost; those are not counted as
 // FP64 evaluations.  The S' in hand is the one formed at xs (the last FP64
@@ -833,7 +837,7 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
     bool need_d = !isfinite(dF0);
     double dF = need_d ? -1.0 : dF0;
     double xsrc = xdF0, rsrc = need_d ? INFINITY : rel0;
-    double cSs = need_d ? 0.0 : -1.0 - dF0 - ca / xdF0 / xdF0;   // c S' at xsrc
+    double KSs = need_d ? 0.0 : dF0 - kappa + ca / xdF0 / xdF0;   // K S' at xsrc
     double xa = NAN, Fa = 0.0, dFa = 0.0, Ha = -1.0;
     for (;;) {
         // the first trial point: x0 when the caller has one inside the bracket
@@ -857,7 +861,7 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
                 if (need_d) {
                     xsrc = x;
                     rsrc = 0x1p-40;
-                    cSs = -1.0 - dF - ca / x / x;
+                    KSs = dF - kappa + ca / x / x;
                 }
                 Ha = -1.0;
                 if (isfinite(ca) && isfinite(rsrc)) {
@@ -865,11 +869,11 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
                     const double dist = fabs(x - xsrc);
                     const double drel = rsrc + 4.0 * dist / rho;
                     double H = 0x1p-27 * rho;
-                    if (fabs(cSs) > 0.0) H = fmin(H, 0.25 * err / (drel * fabs(cSs)));
+                    if (fabs(KSs) > 0.0) H = fmin(H, 0.25 * err / (drel * fabs(KSs)));
                     if (dist <= 0.125 * rho && H > 0.0) {
                         xa = x;
                         Fa = F;
-                        dFa = -1.0 - cSs - ca / x / x;
+                        dFa = kappa + KSs - ca / x / x;
                         dF = dFa;
                         Ha = H;
                     }
@@ -1231,9 +1235,9 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
         return buf ? secular_sum_stored(buf, R.m, T, x) : secular_sum(R, T, shift, -1, x);
     };
     auto PHI = [&](double x) { return fma(rho, S0(x) - rcp(x), 1.0); };
-    // (no FP32 opening here: with a shift next to lambda, nu ~ 1/(lambda - shift)
-    // is far outside what a power-of-two rescaled FP32 copy can represent, and
-    // these solves are a few per cent of all eigenpairs)
+    // (no FP32 bracket here: with a shift next to lambda, nu ~ 1/(lambda - shift)
+    // is far outside what a power-of-two rescaled FP32 copy can represent; the
+    // double-float steps below scale per evaluation instead)
     int it = 0, itd = 0;
     if (o.finish == 1) {
         // the Newton finish on dir * phi, which decreases through the zero; the
@@ -1255,9 +1259,38 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
             err = 0x1p-52 * (1.0 + fabs(rho) * (fabs(S.x) + fabs(rx)));
             return sg * fma(rho, S.x - rx, 1.0);
         };
+        // under AE_FP32_BRACKET, model steps with S in double-float and S' in
+        // compensated FP32 on the stored pairs (no FP32 copy of this problem
+        // is needed) choose the first FP64 trial point, from the middle of the
+        // bracket, and seed the local expansion (K = sign rho, so ca = -sign rho)
+        double x0 = NAN, dF0 = NAN, xdF0 = NAN, rel0 = INFINITY;
+        if (o.precision == 1 && buf) {
+            const int kc = ilogb(fmax(A.P.hi, A.Q.hi));
+            double x = 0.5 * (left + right);
+            for (int t = 0; t < 3 && x != 0.0 && isfinite(x); ++t) {
+                bool ok;
+                const double2 Sd = secular_sum_df_stored(buf, R.m, T, x, ilogb(x), kc, ok);
+                if (!ok) break;
+                const double rx = rcp(x);
+                const double F = sg * fma(rho, Sd.x - rx, 1.0);
+                const double dF = sg * rho * fma(rx, rx, Sd.y);
+                const double d0 = fabs(x - pole);
+                const double beta = -dF * d0 * d0;
+                const double a = F + (side > 0 ? -beta : beta) / d0;
+                const double xn = pole - beta / a;
+                if (!(xn > left && xn < right)) break;
+                xdF0 = x;
+                dF0 = dF;
+                rel0 = 0x1p-18;
+                x0 = xn;
+                const double step = fabs(xn - x);
+                x = xn;
+                if (step < 0x1p-30 * fabs(x)) break;
+            }
+        }
         bool fb;
         it = newton_finish(FD, side, pole, 0.0, left, right, true, true, o.max_iter, left, right,
-                           fb, NAN, &itd);
+                           fb, dF0, &itd, x0, -sg * rho, xdF0, rel0);
     } else {
         double mid = 0.5 * (left + right);
         while (right - left > TWO_EPS * fabs(mid) && it < o.max_iter) {
