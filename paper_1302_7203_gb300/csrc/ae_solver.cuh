@@ -1058,7 +1058,12 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
         // rescaled FP32 copy (F and F' with c S(x) = K T(y)) give the first
         // FP64 trial point; they move no bracket end (unverified)
         double x0 = NAN, dF0 = NAN;
-        if (f32) {
+        // a bracket already narrower than 2^-26 relative needs no FP32 steps:
+        // the double-float step below starts from its middle
+        const bool tight = right - left < 0x1p-26 * fabs(0.5 * (left + right));
+        if (f32 && tight) {
+            x0 = 0.5 * (left + right);
+        } else if (f32) {
             const double big = fmax(fabs(left), fabs(right));
             const double s = ldexp(1.0, ilogb(big));
             const double scd = s / R.f32_scale();
