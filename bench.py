@@ -562,7 +562,8 @@ def main():
                               for k in ("ms_reduce", "ms_eig", "ms_fix", "ms_vectors")},
                 "solver": {k: info[k] for k in ("n_nearzero", "n_otherpole", "n_dpr1shift",
                                                 "n_capped", "max_iter_used", "total_iter",
-                                                "fix_iter", "max_Kb", "max_Knu")}}
+                                                "fix_iter", "total_deriv", "n_ddb",
+                                                "n_mid64", "max_Kb", "max_Knu")}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

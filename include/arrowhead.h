@@ -72,7 +72,15 @@ extern "C" {
                                  not settled by its FP32 evaluation and ran in FP64 */
 
 typedef struct ae_opts {
-    int precision;     /* AE_FP64 (default) or AE_FP32_BRACKET */
+    int precision;     /* AE_FP64 (default): every step in FP64 (double-double
+                          where the paper asks).  AE_FP32_BRACKET: FP32 where its
+                          result is certified or only picks trial points --
+                          Algorithm 1's midpoint test in FP32 with an error
+                          bound (FP64 where the bound leaves the sign open, flag
+                          AE_FLAG_MID64), bisection's opening bracket in FP32
+                          with both ends checked in FP64, and the Newton
+                          finish's first trial point from FP32 and double-float
+                          model steps.  Bracket ends are always FP64 evaluations. */
     double knu_max;    /* K_nu above which Remark 2 is applied; default 10 */
     int max_iter;      /* bisection iteration cap per eigenpair; default 2200 */
     int fixup;         /* 1 (default): Remarks 1 and 2; 0: Algorithm 1 only */
@@ -81,10 +89,12 @@ typedef struct ae_opts {
     int finish;        /* AE_FINISH_BISECT (default) or AE_FINISH_NEWTON.  Newton
                           keeps a sign-change bracket of the same Pick function,
                           every trial point inside it, and Algorithm 3's stop test
-                          (right - left <= 2 eps |mid|, nu = right); it falls back
-                          to bisection when a step leaves the bracket or after 12
-                          steps.  Not in the paper: a faster finish to the same
-                          tolerance.  DPR1-shift remedies always bisect. */
+                          (right - left <= 2 eps |mid|, nu = right); trial points
+                          come from a one-pole model of the function, and points
+                          within a certified radius of an FP64 evaluation are
+                          evaluated from its local expansion F(x) + h F'(x) at
+                          the same error bound.  Not in the paper: a faster finish
+                          to the same tolerance, for the remedies too. */
     int bgate;         /* 0 (default): the element b of Eq. (b_ob) always in
                           double-double.  1: Algorithm 5's gates -- b in
                           standard precision unless the spike ratio
