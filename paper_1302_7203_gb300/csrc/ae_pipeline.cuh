@@ -582,7 +582,21 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
         // input rows); pass 2 scales in place.
         double *keep = stage ? stage : col;      // pass-1 values, RS doubles a row
         double s = 0.0;
-        for (int q = lane; q < n1; q += Team::size) {
+        int q0 = lane;
+        if (!CPLX && !TWO) {
+            // two rows a lane at a time, two independent sums
+            double s1 = 0.0;
+            for (; q0 + Team::size < n1; q0 += 2 * Team::size) {
+                const int ra = S.perm[q0], rb = S.perm[q0 + Team::size];
+                const double xa = comp(ra), xb = comp(rb);
+                keep[ra] = xa;
+                keep[rb] = xb;
+                s = fma(xa, xa, s);
+                s1 = fma(xb, xb, s1);
+            }
+            s += s1;
+        }
+        for (int q = q0; q < n1; q += Team::size) {
             const int r = S.perm[q];
             if (CPLX || TWO) {
                 const double t = recip(r);

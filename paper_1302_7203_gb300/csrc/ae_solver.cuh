@@ -597,7 +597,7 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
     int c1 = 0, c2 = 0;
     double pmax = -INFINITY, pmin = INFINITY, up = -INFINITY, lo = INFINITY, wsum = 0.0,
            usq = 0.0;
-    auto term = [&](int j, double &dhi) -> dd {
+    auto term = [&](int j, double &dhi, double &uacc) -> dd {
         dd del;
         double q1, q2 = 0.0, p;
         if (DD) {
@@ -621,7 +621,7 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
             lo = fmin(lo, fma(-aw, wscale, p));
             wsum += aw;
         }
-        usq = fma(q1, p, usq);                          // zeta_j^2 / delta_j^2
+        uacc = fma(q1, p, uacc);                        // zeta_j^2 / delta_j^2
         dhi = del.hi;
         return dd{q1, q2};
     };
@@ -637,15 +637,37 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
         }
     };
     double dhi;
-    if (skip >= 0 || q >= 0) {
+    if (!DD && (skip >= 0 || q >= 0)) {
+        // standard precision: two interleaved accumulators per range, so that
+        // consecutive terms are independent
         const int e1 = skip >= 0 ? skip : q, b2 = skip >= 0 ? skip + 1 : q;
-        for (int j = T.rank; j < e1; j += Team::size) add(s1, c1, term(j, dhi));
+        double a0 = 0.0, a1 = 0.0, u1 = 0.0;
+        int j = T.rank;
+        for (; j + Team::size < e1; j += 2 * Team::size) {
+            a0 += term(j, dhi, usq).hi;
+            a1 += term(j + Team::size, dhi, u1).hi;
+        }
+        if (j < e1) a0 += term(j, dhi, usq).hi;
+        s1.hi = a0 + a1;
+        a0 = a1 = 0.0;
+        j = b2 + ((T.rank - b2) % Team::size + Team::size) % Team::size;
+        for (; j + Team::size < R.m; j += 2 * Team::size) {
+            a0 += term(j, dhi, usq).hi;
+            a1 += term(j + Team::size, dhi, u1).hi;
+        }
+        if (j < R.m) a0 += term(j, dhi, usq).hi;
+        s2.hi = a0 + a1;
+        usq += u1;
+        if (buf && skip >= 0 && skip % Team::size == T.rank) buf[skip] = make_double2(0.0, 0.0);
+    } else if (skip >= 0 || q >= 0) {
+        const int e1 = skip >= 0 ? skip : q, b2 = skip >= 0 ? skip + 1 : q;
+        for (int j = T.rank; j < e1; j += Team::size) add(s1, c1, term(j, dhi, usq));
         int j = b2 + ((T.rank - b2) % Team::size + Team::size) % Team::size;
-        for (; j < R.m; j += Team::size) add(s2, c2, term(j, dhi));
+        for (; j < R.m; j += Team::size) add(s2, c2, term(j, dhi, usq));
         if (buf && skip >= 0 && skip % Team::size == T.rank) buf[skip] = make_double2(0.0, 0.0);
     } else {
         for (int j = T.rank; j < R.m; j += Team::size) {
-            const dd t = term(j, dhi);
+            const dd t = term(j, dhi, usq);
             if (dhi > 0.0) add(s1, c1, t);
             else add(s2, c2, t);
         }
