@@ -163,9 +163,12 @@ __global__ void k_fix_decide(Kind kind, Scratch S, double knu_max) {
     if (fix_decide_item(kind, S, k, knu_max)) S.fixlist[atomicAdd(S.cnt + C_NFIX, 1)] = k;
 }
 
-// Remedy solves: one CTA (8 warps) per listed eigenpair, so that the few
-// eigenpairs that need one still fill the GPU.
-// With va.fused the same CTA rewrites the remedied eigenpair's column (its
+// Remedy solves.  With few remedies, one CTA (8 warps) per listed eigenpair,
+// so that they still fill the GPU; with at least a quarter as many as the
+// grid has warps, one warp per eigenpair, each on its own stored-pair slice
+// (the grid never exceeds k_eig's, so the slices exist), remedy w on warp
+// w / CTAs of CTA w mod CTAs: spread over all SMs.
+// With va.fused the same team rewrites the remedied eigenpair's column (its
 // position recorded in pos0, as k_eig does).
 template <Kind K, Kind VK>
 __global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o, VecArgs va) {
@@ -174,9 +177,34 @@ __global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o, VecAr
     const int m = S.cnt[C_M];
     const int nfix = S.cnt[C_NFIX];
     const auto R = PolesOf<K>::make(S, m);
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    if ((long long)nfix * 4 >= nwarps) {
+        const int lane = threadIdx.x & 31;
+        const WarpTeam T{lane};
+        const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        double2 *buf = S.wbuf ? S.wbuf + gw * S.wstride : nullptr;
+        // (tickets would hand consecutive remedies to the warps of the first
+        // CTAs to arrive, on a few SMs)
+        const int wi = threadIdx.x >> 5;
+        for (long long w = (long long)wi * gridDim.x + blockIdx.x; w < nfix;
+             w += (long long)(blockDim.x >> 5) * gridDim.x) {
+            const int k = S.fixlist[w];
+            fix_solve_item<K>(R, T, S, k, o, buf);
+            if (va.fused) {
+                __syncwarp();
+                if (lane == 0) {
+                    place_item(S, k);
+                    S.pos0[k] = S.pos[k];
+                }
+                __syncwarp();
+                vector_item<VK>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn,
+                                S, va.out, k, T, (double *)buf);
+            }
+        }
+        return;
+    }
     const CtaTeam<8> T{(int)threadIdx.x, red};
     // k_eig has finished with the stored-pair buffer: one slice per CTA here
-    // (the grid never exceeds k_eig's warp count)
     double2 *buf = S.wbuf ? S.wbuf + (long long)blockIdx.x * S.wstride : nullptr;
     for (;;) {
         __syncthreads();
@@ -338,7 +366,7 @@ static void launch_pipeline(int n, Scratch S, const SolveOpts &so, const RunOpts
     if (ro.ev[2]) cudaEventRecord(ro.ev[2], st);
     if (ro.fixup) {
         k_fix_decide<<<(n + 255) / 256, 256, 0, st>>>(K, S, ro.knu_max);
-        const int fgrid = n < sms * 4 ? n : sms * 4;
+        const int fgrid = n < grid ? n : grid;
         k_fix_solve<K, VK><<<fgrid, 256, 0, st>>>(S, so, va);
     }
     if (ro.ev[3]) cudaEventRecord(ro.ev[3], st);

@@ -581,34 +581,28 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
         // x^2 in sorted order (so the norm does not depend on the order of the
         // input rows); pass 2 scales in place.
         double *keep = stage ? stage : col;      // pass-1 values, RS doubles a row
-        double s = 0.0;
-        int q0 = lane;
-        if (!CPLX && !TWO) {
-            // two rows a lane at a time, two independent sums
-            double s1 = 0.0;
-            for (; q0 + Team::size < n1; q0 += 2 * Team::size) {
-                const int ra = S.perm[q0], rb = S.perm[q0 + Team::size];
-                const double xa = comp(ra), xb = comp(rb);
-                keep[ra] = xa;
-                keep[rb] = xb;
-                s = fma(xa, xa, s);
-                s1 = fma(xb, xb, s1);
-            }
-            s += s1;
-        }
-        for (int q = q0; q < n1; q += Team::size) {
-            const int r = S.perm[q];
+        // two rows a lane at a time, two independent sums (the same order for
+        // every kind, so that real spikes give the real solver's bits)
+        auto one = [&](int r, double &acc) {
             if (CPLX || TWO) {
                 const double t = recip(r);
                 keep[RS * r] = t;
                 const double x = spk[r] * t;
-                s = fma(x, x, s);
+                acc = fma(x, x, acc);
             } else {
                 const double x = comp(r);
                 keep[r] = x;
-                s = fma(x, x, s);
+                acc = fma(x, x, acc);
             }
+        };
+        double s = 0.0, s1 = 0.0;
+        int q0 = lane;
+        for (; q0 + Team::size < n1; q0 += 2 * Team::size) {
+            one(S.perm[q0], s);
+            one(S.perm[q0 + Team::size], s1);
         }
+        if (q0 < n1) one(S.perm[q0], s);
+        s += s1;
         s = T.sum(s) + (last_row ? 1.0 : 0.0);
         double inv, scale = 1.0;
         bool stored = true;

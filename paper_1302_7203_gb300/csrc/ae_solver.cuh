@@ -360,8 +360,9 @@ __device__ __forceinline__ double2 secular_sum_d_stored(const double2 *buf, int 
 // (relative error ~2^-44), added to a Neumaier sum; S' adds q (delta_j r), all
 // of one sign, with Kahan compensation (relative error below 2^-20).  Terms
 // whose scaled delta_j or c_j falls outside 2^+-100 contribute below
-// 2^-100 of the largest.  Returns (S, S') unscaled; `ok` is false when a
-// result is not finite or S is too small for those bounds.
+// 2^-97 each (near the zero |x delta_j r_j| <= 2).  Returns (S, S') unscaled;
+// `ok` is false when a result is not finite or S or S' is below 2^-60 (scaled),
+// where those contributions could matter.
 // one term of secular_sum_df_stored, added to (sh + sl) and (dh - dc)
 __device__ __forceinline__ void df_term(double2 a, float xh, float xl, int kx, int kc, float &sh,
                                         float &sl, float &dh, float &dc) {
@@ -413,7 +414,7 @@ __device__ __forceinline__ double2 secular_sum_df_stored(const double2 *buf, int
     if (j < m) df_term(buf[j], xh, xl, kx, kc, sh0, sl0, dh0, dc0);
     const double S = T.sum(((double)sh0 + (double)sl0) + ((double)sh1 + (double)sl1));
     const double Sd = T.sum(((double)dh0 - (double)dc0) + ((double)dh1 - (double)dc1));
-    ok = isfinite(S) && isfinite(Sd) && fabs(S) >= 0x1p-60;
+    ok = isfinite(S) && isfinite(Sd) && fabs(S) >= 0x1p-60 && fabs(Sd) >= 0x1p-60;
     return make_double2(ldexp(S, kc), ldexp(Sd, kc - kx));
 }
 
