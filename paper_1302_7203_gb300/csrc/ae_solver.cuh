@@ -359,10 +359,10 @@ __device__ __forceinline__ double2 secular_sum_d_stored(const double2 *buf, int 
 // (exact product and TwoSum), r = 1/t (FP32 seed and one correction), q = c_j r
 // (relative error ~2^-44), added to a Neumaier sum; S' adds q (delta_j r), all
 // of one sign, with Kahan compensation (relative error below 2^-20).  Terms
-// whose scaled delta_j or c_j falls outside 2^+-100 contribute below
-// 2^-97 each (near the zero |x delta_j r_j| <= 2).  Returns (S, S') unscaled;
-// `ok` is false when a result is not finite or S or S' is below 2^-60 (scaled),
-// where those contributions could matter.
+// whose scaled delta_j or c_j falls outside 2^+-100 contribute below 2^-99
+// each to either sum (near the zero |x delta_j r_j| <= 2).  Returns (S, S')
+// unscaled; `ok` is false when a result is not finite or either scaled sum is
+// below (m + 1) 2^-78, where those contributions could exceed 2^-21 of it.
 // one term of secular_sum_df_stored, added to (sh + sl) and (dh - dc)
 __device__ __forceinline__ void df_term(double2 a, float xh, float xl, int kx, int kc, float &sh,
                                         float &sl, float &dh, float &dc) {
@@ -414,7 +414,8 @@ __device__ __forceinline__ double2 secular_sum_df_stored(const double2 *buf, int
     if (j < m) df_term(buf[j], xh, xl, kx, kc, sh0, sl0, dh0, dc0);
     const double S = T.sum(((double)sh0 + (double)sl0) + ((double)sh1 + (double)sl1));
     const double Sd = T.sum(((double)dh0 - (double)dc0) + ((double)dh1 - (double)dc1));
-    ok = isfinite(S) && isfinite(Sd) && fabs(S) >= 0x1p-60 && fabs(Sd) >= 0x1p-60;
+    const double floor = (double)(m + 1) * 0x1p-78;   // n terms of 2^-99: 2^-21 relative
+    ok = isfinite(S) && isfinite(Sd) && fabs(S) >= floor && fabs(Sd) >= floor;
     return make_double2(ldexp(S, kc), ldexp(Sd, kc - kx));
 }
 
@@ -576,6 +577,7 @@ struct PassA {
     double lo;          // min of 1/delta_j - |w_j|
     double wsum;        // sum |zeta_j / delta_j|
     double usq;         // sum zeta_j^2 / delta_j^2
+    double cabs;        // sum |zeta_j^2 / delta_j| (bounds every |c_j|)
 };
 
 // GERSH = false skips the Gershgorin quantities (pmax, pmin, up, lo, wsum),
@@ -688,6 +690,7 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
         A.pmax = A.pmin = A.up = A.lo = A.wsum = NAN;
     }
     A.usq = T.sum(usq);
+    A.cabs = s1.hi - s2.hi;             // s1 >= 0 >= s2
     const dd a = R.a_dd(shift, skip);   // alpha - shift
     if (a.hi < 0.0) {                   // -a > 0: P = -a + S1, Q = -S2
         A.P = dd_add_same(dd_neg(a), s1);
@@ -1136,9 +1139,9 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
         // expansion of that one FP64 evaluation closes the bracket; its S'
         // (relative error below 2^-18 here) seeds the expansion
         double xdF0 = NAN, rel0 = INFINITY;
-        if (f32 && buf) {
+        if (f32 && buf && A.cabs > 0.0 && isfinite(A.cabs)) {
             // a second step only after a first one longer than 2^-28 |x|
-            const int kc = ilogb(fmax(A.P.hi, A.Q.hi));
+            const int kc = ilogb(A.cabs);
             for (int t = 0; t < 2 && x0 > left && x0 < right && x0 != 0.0; ++t) {
                 bool ok;
                 const double2 Sd = secular_sum_df_stored(buf, R.m, T, x0, ilogb(x0), kc, ok);
@@ -1294,8 +1297,8 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
         // is needed) choose the first FP64 trial point, from the middle of the
         // bracket, and seed the local expansion (K = sign rho, so ca = -sign rho)
         double x0 = NAN, dF0 = NAN, xdF0 = NAN, rel0 = INFINITY;
-        if (o.precision == 1 && buf) {
-            const int kc = ilogb(fmax(A.P.hi, A.Q.hi));
+        if (o.precision == 1 && buf && A.cabs > 0.0 && isfinite(A.cabs)) {
+            const int kc = ilogb(A.cabs);
             double x = 0.5 * (left + right);
             for (int t = 0; t < 3 && x != 0.0 && isfinite(x); ++t) {
                 bool ok;
