@@ -158,6 +158,22 @@ def test_newton_dpr1_and_svd(ae, n):
                   n, what=f"newton svd n={n} (U)")
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_many_remedies_one_warp_each(ae, precision):
+    # K_nu > 1 sends about a third of the eigenpairs to Remark 2: more than a
+    # quarter of the remedy grid's warps (at most 3648 on 152 SMs), so the
+    # remedy kernel gives each its own warp (with few remedies it uses a CTA
+    # each); same parity bar
+    d, z, a = W.uniform_arrow(4000, seed=51)
+    o = opts(ae, precision)
+    o.knu_max = 1.0
+    g = solve(ae, d, z, a, o)
+    info = g["info"]
+    assert info["n_otherpole"] + info["n_dpr1shift"] >= 1000
+    assert_parity(g["lam"], g["V"], oracle.arrow_eig(d, z, a), len(d) + 1,
+                  what=f"many remedies p={precision}")
+
+
 def test_newton_batched(ae):
     sizes = W.batch_sizes(40, lo=2, hi=900, seed=44)
     inst = [W.uniform_arrow(int(n), seed=4400 + i) for i, n in enumerate(sizes)]
