@@ -1139,13 +1139,12 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
         // expansion of that one FP64 evaluation closes the bracket; its S'
         // (relative error below 2^-18 here) seeds the expansion
         double xdF0 = NAN, rel0 = INFINITY;
-        if (f32 && buf && A.cabs > 0.0 && isfinite(A.cabs)) {
-            // a second step only after a first one longer than 2^-28 |x|
-            const int kc = ilogb(A.cabs);
-            for (int t = 0; t < 2 && x0 > left && x0 < right && x0 != 0.0; ++t) {
-                bool ok;
-                const double2 Sd = secular_sum_df_stored(buf, R.m, T, x0, ilogb(x0), kc, ok);
-                if (!ok) break;
+        if (f32 && buf && A.cabs > 0.0 && isfinite(A.cabs) && x0 > left && x0 < right &&
+            x0 != 0.0) {
+            bool ok;
+            const double2 Sd =
+                secular_sum_df_stored(buf, R.m, T, x0, ilogb(x0), ilogb(A.cabs), ok);
+            if (ok) {
                 const double rx = rcp(x0);
                 const double F = (b - x0) - c * (Sd.x - rx);
                 const double dF = -1.0 - c * fma(rx, rx, Sd.y);
@@ -1155,13 +1154,12 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                 double xs, xb;
                 quad_roots(a, pole, beta, xs, xb);
                 const double xn = side > 0 ? xb : xs;
-                if (!(xn > left && xn < right && fabs(xn - x0) <= 0x1p-8 * d0)) break;
-                xdF0 = x0;
-                dF0 = dF;
-                rel0 = 0x1p-18;
-                const double step = fabs(xn - x0);
-                x0 = xn;
-                if (step <= 0x1p-28 * fabs(xn)) break;
+                if (xn > left && xn < right && fabs(xn - x0) <= 0x1p-8 * d0) {
+                    xdF0 = x0;
+                    dF0 = dF;
+                    rel0 = 0x1p-18;
+                    x0 = xn;
+                }
             }
         }
         bool fb;
