@@ -66,7 +66,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
 # roofline's traffic only while the form, n and sources match.
 KEIG_TRAFFIC = {"form": "fp32_newton_gated", "n": 16384,
                 "read": 11312296960, "write": 8553951488,
-                "src_sha256": "b3f1b98ec962d74647643c5ce2e6777ab033eaa34ef641f9144bbd18a2413b54"}
+                "src_sha256": "2314eb003cadf94aa5bd37e1455cc8c22230495a9c393ee842b94bd36f7bdd5d"}
 
 
 def csrc_sha256():

@@ -1,9 +1,13 @@
 // ae_solver.cuh -- one eigenpair per team (a warp, or a CTA of NW warps):
-// shift selection (Algorithm 1), the inverse of the shifted arrowhead with its
-// element b in double-double (Algorithm 2, Eq. invAi / b_ob, Theorem 6),
-// bisection for the inverse's extreme eigenvalue (Algorithm 3), optionally
-// opened by an FP32 bracket, and the Remark 1 / Remark 2(b) solve on the DPR1
-// inverse (A - sigma I)^{-1}.
+// shift selection (Algorithm 1; its midpoint test optionally in FP32 with an
+// error bound), the inverse of the shifted arrowhead with its element b in
+// double-double or, under Algorithm 5's gate, in standard precision
+// (Algorithm 2, Eq. invAi / b_ob, Theorem 6), the inverse's extreme eigenvalue
+// by bisection (Algorithm 3, optionally opened by an FP32 bracket) or by the
+// bracketed Newton finish on the same function (optionally opened by FP32 and
+// double-float model steps, closed by the local expansion of an FP64
+// evaluation), and the Remark 1 / Remark 2(b) solve on the DPR1 inverse
+// (A - sigma I)^{-1}.
 //
 // Notation (0-based): reduced poles p_0 > p_1 > ... > p_{m-1}, spikes
 // zeta_j > 0, corner alpha; eigenvalue k (k = 0..m) lies in (p_k, p_{k-1}).
