@@ -114,6 +114,10 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the DPR1 / SVD / batched / serving measurements")
     p.add_argument("--serve-requests", type=int, default=120)
+    p.add_argument("--batch-only", type=int, default=0, metavar="COUNT",
+                   help="profiling aid: run only the batched plan on the first COUNT "
+                        "instances of the 4096-instance set (2 warm-up runs, 1 timed) "
+                        "and print one line about it")
     return p.parse_args()
 
 
@@ -435,6 +439,23 @@ def main():
     from paper_1302_7203_gb300 import arrowhead, build, shard, workloads as W
     build.build()
     torch.cuda.set_device(local)
+    if args.batch_only > 0:
+        inst = W.uniform_batch(4096, seed=2)[:args.batch_only]
+        st = torch.cuda.current_stream()
+        B = arrowhead.Batch(inst, opts=form_opts(arrowhead, args.form), stream=st)
+        for _ in range(2):
+            B.run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        B.run()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"mode": "batch_only", "instances": len(inst),
+                          "eigenpairs": int(B.n_off[-1]), "ms": ms,
+                          "eigenpairs_per_s": int(B.n_off[-1]) / (ms / 1e3)}), flush=True)
+        B.close()
+        return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = args.n
