@@ -17,6 +17,17 @@ def tolerance(n, factor=10.0):
     return factor * n * EPS64
 
 
+def widened(orc, n, factor=10.0):
+    """Mask of the eigenvalues whose comparison the oracle's own bound widens:
+    where 4 abserr exceeds factor n eps64 |lambda|, lam_errors divides by the
+    bound instead of |lambda|.  Full-size checks assert that this mask is
+    empty, so that no comparison there relaxes silently; the only expected
+    member elsewhere is an exactly zero eigenvalue (relative error undefined)."""
+    lam_or = np.abs(orc["lam"])
+    absb = orc.get("abserr", np.zeros_like(lam_or))
+    return 4 * absb / tolerance(n, factor) > lam_or
+
+
 def lam_errors(lam_gpu, orc, n):
     lam_or = orc["lam"]
     scale = np.abs(lam_or)

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from conftest import read_golden
-from parity import assert_parity, tolerance
+from parity import assert_parity, tolerance, widened
 from paper_1302_7203_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -217,6 +217,7 @@ def test_graded_full_size_sampled(ae):
     ks = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1],
                                    rng.choice(n, 96, replace=False), fixed[:64]]))
     o = oracle.arrow_eig(d, z, a, ks=ks)
+    assert not widened(o, n).any()   # every comparison at the full 10 n eps64 bar
     assert_parity(lam[ks], V[:, ks], o, n, cols=ks, what="graded n=16384 sampled")
     # orthogonality of the sampled columns
     G = V[:, ks].T @ V[:, ks] - np.eye(ks.size)
@@ -275,4 +276,5 @@ def test_fp32_bracket_full_size_sampled(ae):
     ks = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1],
                                    rng.choice(n, 96, replace=False), fixed[:32], fb[:32]]))
     o = oracle.arrow_eig(d, z, a, ks=ks)
+    assert not widened(o, n).any()   # every comparison at the full 10 n eps64 bar
     assert_parity(lam[ks], V[:, ks], o, n, cols=ks, what="fp32 bracket graded n=16384")

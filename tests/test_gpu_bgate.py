@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 from conftest import read_golden
-from parity import assert_parity, lam_errors
+from parity import assert_parity, lam_errors, widened
 from paper_1302_7203_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -52,14 +52,15 @@ def case(name):
     return W.mirrored_arrow(41)
 
 
-@pytest.mark.parametrize("finish", [0, 1])
+@pytest.mark.parametrize("form", [(0, 0), (0, 1), (1, 1)])     # (precision, finish)
 @pytest.mark.parametrize("name", ["ex1", "ex2", "ex3", "uniform1000", "graded3001", "qdot",
                                   "mirrored"])
-def test_gated_parity(ae, name, finish):
+def test_gated_parity(ae, name, form):
     d, z, a = case(name)
-    g, dg, info = solve(ae, d, z, a, ae.default_opts(bgate=1, finish=finish))
+    g, dg, info = solve(ae, d, z, a, ae.default_opts(bgate=1, precision=form[0],
+                                                     finish=form[1]))
     o = oracle.arrow_eig(d, z, a)
-    assert_parity(g["lam"], g["V"], o, len(d) + 1, what=f"bgate {name} finish {finish}")
+    assert_parity(g["lam"], g["V"], o, len(d) + 1, what=f"bgate {name} form {form}")
     assert info["n_capped"] == 0
     # every eigenpair whose b went to double-double is flagged, and counted
     assert info["n_ddb"] >= int(np.count_nonzero(dg["flags"] & ae.FLAG_DDB))
@@ -119,4 +120,5 @@ def test_gated_full_size_sampled(ae):
     ks = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1], rng.choice(n, 64, False),
                                    ddb[:32], fixed[:32], risky]))
     o = oracle.arrow_eig(d, z, a, ks=ks)
+    assert not widened(o, n).any()   # every comparison at the full 10 n eps64 bar
     assert_parity(lam[ks], V[:, ks], o, n, cols=ks, what="bgate graded n=16384 sampled")

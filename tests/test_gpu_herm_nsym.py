@@ -46,7 +46,8 @@ def nsym(ae, d, zc, zr, a, **kw):
     return r["lam"].cpu().numpy(), r["X"].cpu().numpy(), r["Y"].cpu().numpy(), r["info"]
 
 
-FORMS = [(0, 0), (1, 0), (0, 1)]     # (precision, finish)
+# (precision, finish, bgate); the last is the benchmarked form
+FORMS = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 1)]
 
 
 def herm_case(case):
@@ -72,7 +73,7 @@ def test_herm_parity(ae, case, form):
     d, z, a = herm_case(case)
     o = oracle.herm_eig(d, z, a)
     o["V"] = o["U"]
-    lam, U, info = herm(ae, d, z, a, opts=ae.default_opts(precision=form[0], finish=form[1]))
+    lam, U, info = herm(ae, d, z, a, opts=ae.default_opts(precision=form[0], finish=form[1], bgate=form[2]))
     assert_parity(lam, U, o, len(d) + 1, what=f"herm {case} form {form}")
     assert info["n_capped"] == 0
 
@@ -133,7 +134,7 @@ def test_nsym_parity(ae, case, form):
     d, zc, zr, a = nsym_case(case)
     o = oracle.nsym_eig(d, zc, zr, a)
     lam, X, Y, info = nsym(ae, d, zc, zr, a,
-                           opts=ae.default_opts(precision=form[0], finish=form[1]))
+                           opts=ae.default_opts(precision=form[0], finish=form[1], bgate=form[2]))
     n = len(d) + 1
     o["V"] = o["X"]
     assert_parity(lam, X, o, n, what=f"nsym {case} form {form} (X)")

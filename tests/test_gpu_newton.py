@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import assert_parity
+from parity import assert_parity, widened
 from paper_1302_7203_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -70,13 +70,17 @@ def case_data(case):
     return d, z, 0.3
 
 
+@pytest.mark.parametrize("gate", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("case", CASES)
-def test_newton_parity(ae, case, precision):
+def test_newton_parity(ae, case, precision, gate):
     d, z, a = case_data(case)
-    g = solve(ae, d, z, a, opts(ae, precision))
+    o_ = opts(ae, precision)
+    o_.bgate = gate
+    g = solve(ae, d, z, a, o_)
     o = oracle.arrow_eig(d, z, a)
-    assert_parity(g["lam"], g["V"], o, len(d) + 1, what=f"newton p={precision} {case}")
+    assert_parity(g["lam"], g["V"], o, len(d) + 1,
+                  what=f"newton p={precision} gate={gate} {case}")
     assert g["info"]["n_capped"] == 0
 
 
@@ -133,6 +137,7 @@ def test_newton_full_size_sampled(ae):
     ks = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1],
                                    rng.choice(n, 96, replace=False), fixed[:32], fb[:32]]))
     o = oracle.arrow_eig(d, z, a, ks=ks)
+    assert not widened(o, n).any()   # every comparison at the full 10 n eps64 bar
     assert_parity(lam[ks], V[:, ks], o, n, cols=ks, what="newton graded n=16384 sampled")
     assert g["info"]["total_iter"] < 6 * n
 
@@ -189,7 +194,7 @@ def test_newton_batched(ae):
 
 
 @pytest.mark.parametrize("e", [-400, -300, 300, 400])
-@pytest.mark.parametrize("form", [(0, 0, 0), (0, 1, 1), (1, 1, 0)])
+@pytest.mark.parametrize("form", [(0, 0, 0), (0, 1, 1), (1, 1, 0), (1, 1, 1)])
 def test_extreme_power_of_two_scaling(ae, e, form):
     # A -> 2^e A scales every eigenvalue by 2^e and leaves the vectors, exactly,
     # as long as the squares the solve forms (zeta^2, delta^2, 1/zeta_i^2) stay
