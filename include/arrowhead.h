@@ -49,7 +49,8 @@ extern "C" {
 #define AE_ERR_CUDA 1001      /* a CUDA runtime call failed (see ae_last_cuda_error) */
 #define AE_ERR_INPUT 1002     /* device-side check: non-finite d, z or alpha */
 #define AE_ERR_NOCONV 1003    /* some eigenpair reached opts->max_iter */
-#define AE_ERR_TOO_LARGE 1004 /* arrow_eig_noalloc: n exceeds its static scratch */
+#define AE_ERR_TOO_LARGE 1004 /* arrow_eig_noalloc: n exceeds its static scratch;
+                                 arrow_eig_part: the part's items exceed cap */
 
 /* precision of the bisection (see ae_opts.precision) */
 #define AE_FP64 0             /* all-FP64 bisection from the Gershgorin bracket */
@@ -130,6 +131,10 @@ typedef struct ae_info {
                               the derivative */
     int n_mid64;          /* with AE_FP32_BRACKET: midpoint tests (Algorithm 1) that
                              needed their FP64 pass (flag AE_FLAG_MID64) */
+    long long n_f32_passes; /* with AE_FP32_BRACKET: O(n) passes evaluated in FP32
+                             (midpoint tests, model steps, bracket bisection) */
+    long long n_df_passes;  /* with AE_FP32_BRACKET: O(n) passes in double-float
+                             (the Newton finish's opening model steps) */
 } ae_info;
 
 /* Optional per-eigenpair diagnostics (device arrays of length n, any may be
@@ -186,6 +191,51 @@ const char *ae_last_cuda_error(void);
 int arrow_eig(int n, const double *d, const double *z, double alpha,
               double *lambda, double *V, int ldv, double *shift, double *mu,
               const ae_opts *opts, ae_info *info, const ae_diag *diag, void *stream);
+
+/*
+ * arrow_eig_part -- one part of arrow_eig split across devices or calls.
+ * Eigenpairs are independent once the reduction is done (Sec. 1: each comes
+ * from the shifted inverse of its own nearest pole, O(n) work apiece), so one
+ * instance splits by eigenpair ranges with nothing exchanged: every part
+ * repeats the O(n log n) reduction of the whole input (Sec. 1: order, zero
+ * spikes, equal poles) and then solves
+ *   - the computed eigenpairs k in [k0, k1) of the reduced arrowhead with
+ *     m + 1 computed eigenvalues, k0 = part (m + 1) / nparts and
+ *     k1 = (part + 1) (m + 1) / nparts (integer division), and
+ *   - the deflated rows whose values lie in [p_{k1-1}, p_{k0-1}) (reduced
+ *     poles p; p_{-1} = +inf, p_m = -inf),
+ * which hold the contiguous output positions [*pos0, *pos0 + *count) of the
+ * whole decomposition, in the same descending order.  The remedy decision of
+ * Eq. (K0) for an eigenpair needs the eigenvalues on both sides of it: each
+ * part also solves the eigenpair just outside each end of its range (Algorithm
+ * 1's solve only, which gives the bits the owning part computes), so the
+ * parts' results put side by side equal arrow_eig's, except that a remedied
+ * eigenpair (Remarks 1, 2) may be re-solved by a team of another width and so
+ * agree within the tolerance rather than bit for bit.  The solver's counters
+ * in info include the two edge solves.
+ *
+ *  n, d, z, alpha  the whole arrowhead, as arrow_eig                (args 1-4)
+ *  part, nparts    this part, 0 <= part < nparts                     (args 5, 6)
+ *  lambda  device, cap doubles out: the part's eigenvalues, descending    (7)
+ *  V, ldv  device, ldv*cap doubles out or NULL: their eigenvectors (full
+ *          length n, rows in the caller's input order), ldv >= n     (8, 9)
+ *  cap     room of lambda and V in items; a part with more items returns
+ *          AE_ERR_TOO_LARGE before it solves (arrow_eig_part_size gives the
+ *          count)                                                       (10)
+ *  pos0, count  host out: the part's first output position and item count
+ *          (the call synchronises `stream` after the reduction)  (args 11, 12)
+ *  opts, info, stream: as arrow_eig                           (args 13-15)
+ */
+int arrow_eig_part(int n, const double *d, const double *z, double alpha, int part, int nparts,
+                   double *lambda, double *V, int ldv, int cap, int *pos0, int *count,
+                   const ae_opts *opts, ae_info *info, void *stream);
+
+/* The first output position and item count of part `part` of `nparts` of
+   the arrowhead (d, z) (the reduction only; synchronises `stream`).
+   Arguments as arrow_eig_part: n 1, d 2, z 3, part 4, nparts 5, pos0 6,
+   count 7 (host), stream 8. */
+int arrow_eig_part_size(int n, const double *d, const double *z, int part, int nparts,
+                        int *pos0, int *count, void *stream);
 
 /*
  * dpr1_eig -- all eigenpairs of the diagonal-plus-rank-one matrix
@@ -445,6 +495,17 @@ int arrow_eig_host(int n, const double *d_host, const double *z_host, double alp
 int arrow_eig_noalloc(int n, const double *d, const double *z, double alpha,
                       double *lambda, double *V, int ldv, double *shift, double *mu,
                       const ae_opts *opts, ae_info *info, const ae_diag *diag, void *stream);
+
+/*
+ * ae_fma_peaks -- measured fused multiply-add throughput of this GPU's FP64
+ * and FP32 pipes in TFLOP/s (2 flops per FMA), the denominators of the
+ * solver's roofline.  The paper has no counterpart: it is a measurement aid.
+ * A grid that fills every SM runs independent FMA chains (8 per thread);
+ * each rate is the best of three CUDA-event-timed launches after a warm-up
+ * (about 0.1 s for FP64, 0.04 s for FP32) on `stream`, which the call
+ * synchronises.  Either output pointer (host) may be NULL, not both (-1).
+ */
+int ae_fma_peaks(double *fp64_tflops, double *fp32_tflops, void *stream);
 
 /*
  * ae_debug_rcp -- the solver's FP64 reciprocal (Newton-Raphson refinement of

@@ -37,7 +37,8 @@ EXPORTED = ["ae_default_opts", "ae_status_string", "ae_last_cuda_error", "arrow_
             "ae_batch_run", "ae_batch_info", "ae_batch_destroy", "ae_autotune",
             "ae_team_width", "ae_serve_create", "ae_serve_submit", "ae_serve_poll",
             "ae_serve_result", "ae_serve_release", "ae_serve_stats", "ae_serve_destroy",
-            "arrow_eig_host", "arrow_eig_noalloc", "ae_debug_rcp"]
+            "arrow_eig_host", "arrow_eig_noalloc", "arrow_eig_part", "arrow_eig_part_size",
+            "ae_fma_peaks", "ae_debug_rcp"]
 AE_EAGAIN = 1005
 KIND_ARROW, KIND_DPR1, KIND_SVD = 0, 1, 2
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
@@ -61,7 +62,8 @@ class AeInfo(ctypes.Structure):
                 ("max_Knu", ctypes.c_double), ("ms_reduce", ctypes.c_float),
                 ("ms_eig", ctypes.c_float), ("ms_fix", ctypes.c_float),
                 ("ms_vectors", ctypes.c_float), ("n_ddb", ctypes.c_int),
-                ("total_deriv", ctypes.c_longlong), ("n_mid64", ctypes.c_int)]
+                ("total_deriv", ctypes.c_longlong), ("n_mid64", ctypes.c_int),
+                ("n_f32_passes", ctypes.c_longlong), ("n_df_passes", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,6 +117,12 @@ def lib():
         L.arrow_eig.restype = I
         L.arrow_eig_host.argtypes = [I, P, P, D, P, P, P, P, ctypes.POINTER(AeOpts),
                                      ctypes.POINTER(AeInfo), P]
+        IP = ctypes.POINTER(I)
+        L.arrow_eig_part.argtypes = [I, P, P, D, I, I, P, P, I, I, IP, IP,
+                                     ctypes.POINTER(AeOpts), ctypes.POINTER(AeInfo), P]
+        L.arrow_eig_part.restype = I
+        L.arrow_eig_part_size.argtypes = [I, P, P, I, I, IP, IP, P]
+        L.arrow_eig_part_size.restype = I
         L.arrow_eig_host.restype = I
         L.dpr1_eig.argtypes = [I, P, P, D, P, P, I, ctypes.POINTER(AeOpts),
                                ctypes.POINTER(AeInfo), ctypes.POINTER(AeDiag), P]
@@ -166,6 +174,8 @@ def lib():
         L.ae_serve_destroy.restype = I
         L.arrow_eig_noalloc.argtypes = L.arrow_eig.argtypes
         L.arrow_eig_noalloc.restype = I
+        L.ae_fma_peaks.argtypes = [ctypes.POINTER(D), ctypes.POINTER(D), P]
+        L.ae_fma_peaks.restype = I
         L.ae_debug_rcp.argtypes = [I, P, P, P]
         L.ae_debug_rcp.restype = I
         _lib = L
@@ -256,6 +266,57 @@ def arrow_eig(d, z, alpha, *, vectors=True, want_shift=False, opts=None, info=Fa
         res["info"] = inf.as_dict()
     if diag:
         res["diag"] = dgt
+    return res
+
+
+def arrow_eig_part_size(d, z, part, nparts, stream=None):
+    """(first output position, item count) of part `part` of `nparts` of the
+    arrowhead (d, z) (float64 CUDA tensors of length n-1)."""
+    n = int(d.numel()) + 1
+    p0, cnt = ctypes.c_int(), ctypes.c_int()
+    _check("arrow_eig_part_size", lib().arrow_eig_part_size(
+        n, _ptr(d), _ptr(z), int(part), int(nparts), ctypes.byref(p0), ctypes.byref(cnt),
+        _stream_handle(stream)))
+    return p0.value, cnt.value
+
+
+def arrow_eig_part(d, z, alpha, part, nparts, *, vectors=True, opts=None, info=False,
+                   stream=None, cap=None, out=None):
+    """Part `part` of `nparts` of arrow_eig on the GPU (include/arrowhead.h).
+
+    Returns ``lam`` (the part's eigenvalues, descending), ``V`` (n x count,
+    columns ``V[:, j]``) when ``vectors``, ``pos0`` (the output position of
+    its first item in the whole decomposition) and ``info`` when requested.
+    ``cap`` defaults to the part's exact size (one extra size query); ``out``
+    may supply ``lam`` (cap) and ``V`` (cap x n, row j = column j) tensors."""
+    import torch
+    dev = d.device
+    n = int(d.numel()) + 1
+    out = dict(out or {})
+    if cap is None:
+        cap = (int(out["lam"].numel()) if "lam" in out
+               else arrow_eig_part_size(d, z, part, nparts, stream=stream)[1])
+    lam = out.get("lam")
+    if lam is None:
+        lam = torch.empty(max(cap, 1), dtype=torch.float64, device=dev)
+    V = out.get("V") if vectors else None
+    if vectors and V is None:
+        V = torch.empty((max(cap, 1), n), dtype=torch.float64, device=dev)
+    o = opts if opts is not None else default_opts()
+    inf = AeInfo() if info else None
+    p0, cnt = ctypes.c_int(), ctypes.c_int()
+    st = lib().arrow_eig_part(n, _ptr(d), _ptr(z), float(alpha), int(part), int(nparts),
+                              _ptr(lam), _ptr(V), n, int(cap), ctypes.byref(p0),
+                              ctypes.byref(cnt), ctypes.byref(o),
+                              ctypes.byref(inf) if inf is not None else None,
+                              _stream_handle(stream))
+    _check("arrow_eig_part", st)
+    c = cnt.value
+    res = {"lam": lam[:c], "pos0": p0.value, "count": c}
+    if vectors:
+        res["V"] = V[:c].t()
+    if info:
+        res["info"] = inf.as_dict()
     return res
 
 
@@ -648,6 +709,14 @@ def arrow_eig_host(d, z, alpha, *, vectors=True, want_shift=False, opts=None, st
     return res
 
 
+def fma_peaks(stream=None):
+    """Measured FMA throughput (TFLOP/s) of the FP64 and FP32 pipes."""
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    _check("ae_fma_peaks", lib().ae_fma_peaks(ctypes.byref(f64), ctypes.byref(f32),
+                                              _stream_handle(stream)))
+    return {"fp64_tflops": f64.value, "fp32_tflops": f32.value}
+
+
 def debug_rcp(x, stream=None):
     """The solver's FP64 reciprocal applied elementwise (device tensor)."""
     import torch
@@ -663,9 +732,9 @@ def exported_symbols(path=LIB_PATH):
     return [s for s in EXPORTED if hasattr(L, s)]
 
 
-__all__ = ["arrow_eig", "herm_arrow_eig", "nsym_arrow_eig", "dpr1_eig", "tri_arrow_svd",
+__all__ = ["arrow_eig", "arrow_eig_part", "arrow_eig_part_size", "herm_arrow_eig", "nsym_arrow_eig", "dpr1_eig", "tri_arrow_svd",
            "Batch", "Server", "autotune", "arrow_eig_host",
-           "debug_rcp", "default_opts", "lib", "AeOpts",
+           "fma_peaks", "debug_rcp", "default_opts", "lib", "AeOpts",
            "AeInfo", "AeDiag", "AeError", "exported_symbols", "EXPORTED"]
 
 _ = np  # numpy is used by callers passing host arrays

@@ -105,19 +105,29 @@ const char *ae_status_string(int status) {
         case AE_ERR_NOCONV: return "iteration cap reached";
         case AE_EAGAIN: return "queue full or result not ready (try again)";
         case AE_ERR_TOO_LARGE:
-            return "n too large for the static scratch of arrow_eig_noalloc "
-                   "(AE_NOALLOC_SCRATCH_BYTES)";
+            return "too large: n beyond the static scratch of arrow_eig_noalloc "
+                   "(AE_NOALLOC_SCRATCH_BYTES), or a part's items beyond the room "
+                   "given to arrow_eig_part";
         default: return "unknown status";
     }
 }
 
 const char *ae_last_cuda_error(void) { return g_err; }
 
+// One part of a split arrow_eig (arrow_eig_part): which part, the room the
+// caller's outputs have, and where the part's first output position and item
+// count go.
+struct PartSpec {
+    int part, nparts, cap;
+    int *pos0, *count;
+};
+
 // Shared by arrow_eig, dpr1_eig and tri_arrow_svd: scratch, launch, optional
 // synchronising summary.
 static int solve_common(ae::Kind kind, int n, const double *d, const double *z, double alpha,
                         double rho, const ae::Outputs &out, const ae_opts *opts, ae_info *info,
-                        void *stream, const double *zrow = nullptr) {
+                        void *stream, const double *zrow = nullptr,
+                        const PartSpec *part = nullptr) {
     ae::RunOpts ro;
     if (ae::resolve_opts(opts, ro)) return -10;
     cudaStream_t st = (cudaStream_t)stream;
@@ -142,9 +152,17 @@ static int solve_common(ae::Kind kind, int n, const double *d, const double *z, 
     S.wbuf = (double2 *)wb;
     S.wstride = wstride;
     int status = AE_OK;
-    e = ae::launch_solve(kind, n, d, z, alpha, rho, out, ro, S, st, zrow);
+    bool solved = true;
+    if (part) {
+        e = ae::launch_arrow_part(n, d, z, alpha, part->part, part->nparts, part->cap, out, ro,
+                                  S, st, part->pos0, part->count);
+        solved = out.lambda && *part->count <= part->cap;
+        if (e == cudaSuccess && out.lambda && !solved) status = AE_ERR_TOO_LARGE;
+    } else {
+        e = ae::launch_solve(kind, n, d, z, alpha, rho, out, ro, S, st, zrow);
+    }
     if (e != cudaSuccess) status = cuda_fail(e);
-    if (info && status == AE_OK) {
+    if (info && status == AE_OK && solved) {
         int cnt[ae::C_COUNT];
         unsigned long long c64[ae::C64_COUNT];
         e = cudaMemcpyAsync(cnt, S.cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st);
@@ -170,6 +188,8 @@ static int solve_common(ae::Kind kind, int n, const double *d, const double *z, 
             info->n_ddb = cnt[ae::C_DDB];
             info->n_mid64 = cnt[ae::C_MID64];
             info->total_deriv = (long long)c64[ae::C64_DERIV];
+            info->n_f32_passes = (long long)c64[ae::C64_F32];
+            info->n_df_passes = (long long)c64[ae::C64_DF];
             if (prof.on) {
                 cudaEventElapsedTime(&info->ms_reduce, prof.ev[0], prof.ev[1]);
                 cudaEventElapsedTime(&info->ms_eig, prof.ev[1], prof.ev[2]);
@@ -216,6 +236,42 @@ int arrow_eig(int n, const double *d, const double *z, double alpha, double *lam
     if (V && ldv < n) return -7;
     const ae::Outputs out = make_outputs(lambda, V, ldv, nullptr, 0, shift, mu, diag);
     return solve_common(ae::KIND_ARROW, n, d, z, alpha, 0.0, out, opts, info, stream);
+}
+
+int arrow_eig_part(int n, const double *d, const double *z, double alpha, int part, int nparts,
+                   double *lambda, double *V, int ldv, int cap, int *pos0, int *count,
+                   const ae_opts *opts, ae_info *info, void *stream) {
+    if (n < 1) return -1;
+    if (n > 1 && !d) return -2;
+    if (n > 1 && !z) return -3;
+    if (!isfinite(alpha)) return -4;
+    if (nparts < 1) return -6;
+    if (part < 0 || part >= nparts) return -5;
+    if (!lambda) return -7;
+    if (V && ldv < n) return -9;
+    if (cap < 0) return -10;
+    if (!pos0) return -11;
+    if (!count) return -12;
+    const ae::Outputs out = make_outputs(lambda, V, ldv, nullptr, 0, nullptr, nullptr, nullptr);
+    const PartSpec ps{part, nparts, cap, pos0, count};
+    return solve_common(ae::KIND_ARROW, n, d, z, alpha, 0.0, out, opts, info, stream, nullptr,
+                        &ps);
+}
+
+int arrow_eig_part_size(int n, const double *d, const double *z, int part, int nparts,
+                        int *pos0, int *count, void *stream) {
+    if (n < 1) return -1;
+    if (n > 1 && !d) return -2;
+    if (n > 1 && !z) return -3;
+    if (part < 0 || part >= nparts) return -4;
+    if (nparts < 1) return -5;
+    if (!pos0) return -6;
+    if (!count) return -7;
+    const ae::Outputs out = make_outputs(nullptr, nullptr, n, nullptr, 0, nullptr, nullptr,
+                                         nullptr);
+    const PartSpec ps{part, nparts, 0, pos0, count};
+    return solve_common(ae::KIND_ARROW, n, d, z, 0.0, 0.0, out, nullptr, nullptr, stream,
+                        nullptr, &ps);
 }
 
 int dpr1_eig(int n, const double *d, const double *u, double rho, double *lambda, double *Q,
@@ -340,6 +396,12 @@ int arrow_eig_host(int n, const double *d_host, const double *z_host, double alp
     if (status == AE_OK && e2 != cudaSuccess) status = cuda_fail(e2);
     if (status == AE_OK && e3 != cudaSuccess) status = cuda_fail(e3);
     return status;
+}
+
+int ae_fma_peaks(double *fp64_tflops, double *fp32_tflops, void *stream) {
+    if (!fp64_tflops && !fp32_tflops) return -1;
+    cudaError_t e = ae::probe_fma_rates(fp64_tflops, fp32_tflops, (cudaStream_t)stream);
+    return e == cudaSuccess ? AE_OK : cuda_fail(e);
 }
 
 int ae_debug_rcp(int n, const double *x, double *y, void *stream) {

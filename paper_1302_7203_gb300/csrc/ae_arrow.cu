@@ -133,18 +133,23 @@ template <Kind K, Kind VK>
 __global__ void __launch_bounds__(256, 3) k_eig(Scratch S, SolveOpts o, VecArgs va) {
     const int lane = threadIdx.x & 31;
     const int m = S.cnt[C_M];
-    const int ncomp = m + 1;
     const auto R = PolesOf<K>::make(S, m);
     const WarpTeam T{lane};
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     double2 *buf = S.wbuf ? S.wbuf + gw * S.wstride : nullptr;
+    // a part also solves the eigenpair on each side of its range (Algorithm
+    // 1's solve only, the same bits its owner computes): the remedy decision
+    // of Eq. (K0) needs both neighbours
+    const PartRange P = part_range(S);
+    const int k_lo = P.k0 > 0 ? P.k0 - 1 : 0;
+    const int k_hi = P.k1 <= m ? P.k1 + 1 : m + 1;
     for (;;) {
         int k = 0;
-        if (lane == 0) k = atomicAdd(S.cnt + C_WORK, 1);
+        if (lane == 0) k = k_lo + atomicAdd(S.cnt + C_WORK, 1);
         k = __shfl_sync(FULL, k, 0);
-        if (k >= ncomp) break;
+        if (k >= k_hi) break;
         eig_item<K>(R, T, S, k, o, buf);
-        if (va.fused) {
+        if (va.fused && k >= P.k0 && k < P.k1) {
             __syncwarp();
             if (lane == 0) {
                 place_item(S, k);
@@ -152,33 +157,83 @@ __global__ void __launch_bounds__(256, 3) k_eig(Scratch S, SolveOpts o, VecArgs 
             }
             __syncwarp();
             vector_item<VK>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn, S,
-                            va.out, k, T, (double *)buf);
+                            va.out, k, T, (double *)buf, true, true);
         }
     }
 }
 
-// Remedy decisions: one thread per eigenpair.
-__global__ void k_fix_decide(Kind kind, Scratch S, double knu_max) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (fix_decide_item(kind, S, k, knu_max)) S.fixlist[atomicAdd(S.cnt + C_NFIX, 1)] = k;
+// Remedy decisions: one thread per eigenpair (of the part).  The solves on a
+// DPR1 inverse (Remarks 1, 2(b)), which add a double-double pass, are listed
+// from the front of the n-entry list and the others from its back, so that
+// the remedy kernel deals the costlier ones out first, one per SM in turn.
+__global__ void k_fix_decide(Kind kind, Scratch S, double knu_max, int n) {
+    const PartRange P = part_range(S);
+    const int k = P.k0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.k1) return;
+    const int r = fix_decide_item(kind, S, k, knu_max);
+    if (r == AE_FLAG_OTHERPOLE) S.fixlist[n - 1 - atomicAdd(S.cnt + C_NFIX2, 1)] = k;
+    else if (r) S.fixlist[atomicAdd(S.cnt + C_NFIX, 1)] = k;
 }
 
-// Remedy solves.  With few remedies, one CTA (8 warps) per listed eigenpair,
-// so that they still fill the GPU; with at least a quarter as many as the
-// grid has warps, one warp per eigenpair, each on its own stored-pair slice
-// (the grid never exceeds k_eig's, so the slices exist), remedy w on warp
-// w / CTAs of CTA w mod CTAs: spread over all SMs.
-// With va.fused the same team rewrites the remedied eigenpair's column (its
-// position recorded in pos0, as k_eig does).
+// remedy w of the list k_fix_decide wrote (front part first, then the back)
+__device__ __forceinline__ int fix_at(const Scratch &S, long long w, int n) {
+    const int nf = S.cnt[C_NFIX];
+    return w < nf ? S.fixlist[w] : S.fixlist[n - 1 - (int)(w - nf)];
+}
+
+// Remedy solves by teams of NW warps (NW = 8, 4 or 2) that share their CTA:
+// team g of CTA b takes remedies w = g * grid + b, then w + teams, ... (so that
+// consecutive remedies land on different SMs), each on the stored-pair slice
+// of the team's first warp (the grid never exceeds k_eig's, so the slices
+// exist).  With va.fused the same team rewrites the remedied eigenpair's
+// column (its position recorded in pos0, as k_eig does).
+template <Kind K, Kind VK, int NW>
+__device__ __forceinline__ void fix_solve_teams(const Scratch &S, const SolveOpts &o,
+                                                const VecArgs &va, int nfix, double *red) {
+    constexpr int TPC = 8 / NW;                  // teams per CTA of 8 warps
+    const int m = S.cnt[C_M];
+    const auto R = PolesOf<K>::make(S, m);
+    const int g = (int)(threadIdx.x >> 5) / NW;
+    const CtaTeam<NW> T{(int)threadIdx.x - g * 32 * NW, red + 2 * NW * g, NW == 8 ? 0 : 1 + g};
+    const long long w0 = (long long)blockIdx.x * 8 + (long long)g * NW;
+    double2 *buf = S.wbuf ? S.wbuf + w0 * S.wstride : nullptr;
+    for (long long w = (long long)g * gridDim.x + blockIdx.x; w < nfix;
+         w += (long long)TPC * gridDim.x) {
+        const int k = fix_at(S, w, va.n);
+        const bool kept = fix_solve_item<K>(R, T, S, k, o, buf);
+        if (va.fused) {
+            T.sync();
+            if (T.rank == 0) {
+                place_item(S, k);
+                S.pos0[k] = S.pos[k];
+            }
+            T.sync();
+            vector_item<VK>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn, S,
+                            va.out, k, T, (double *)buf, true, kept);
+        }
+        T.sync();                                // before buf and red are reused
+    }
+}
+
+// Remedy solves.  The team size is the largest of 8, 4, 2 warps that still
+// gives every listed eigenpair a team of its own (one wave over the grid);
+// with more remedies than half the grid's warps, one warp each, remedy w on
+// warp w / CTAs of CTA w mod CTAs: spread over all SMs.
 template <Kind K, Kind VK>
 __global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o, VecArgs va) {
     __shared__ double red[16];
-    __shared__ int ticket;
-    const int m = S.cnt[C_M];
-    const int nfix = S.cnt[C_NFIX];
-    const auto R = PolesOf<K>::make(S, m);
+    const int nfix = S.cnt[C_NFIX] + S.cnt[C_NFIX2];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    if ((long long)nfix * 4 >= nwarps) {
+    if (nfix == 0) return;
+    if (nwarps / 8 >= nfix) {
+        fix_solve_teams<K, VK, 8>(S, o, va, nfix, red);
+    } else if (nwarps / 4 >= nfix) {
+        fix_solve_teams<K, VK, 4>(S, o, va, nfix, red);
+    } else if (nwarps / 2 >= nfix) {
+        fix_solve_teams<K, VK, 2>(S, o, va, nfix, red);
+    } else {
+        const int m = S.cnt[C_M];
+        const auto R = PolesOf<K>::make(S, m);
         const int lane = threadIdx.x & 31;
         const WarpTeam T{lane};
         const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -188,8 +243,8 @@ __global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o, VecAr
         const int wi = threadIdx.x >> 5;
         for (long long w = (long long)wi * gridDim.x + blockIdx.x; w < nfix;
              w += (long long)(blockDim.x >> 5) * gridDim.x) {
-            const int k = S.fixlist[w];
-            fix_solve_item<K>(R, T, S, k, o, buf);
+            const int k = fix_at(S, w, va.n);
+            const bool kept = fix_solve_item<K>(R, T, S, k, o, buf);
             if (va.fused) {
                 __syncwarp();
                 if (lane == 0) {
@@ -198,31 +253,8 @@ __global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o, VecAr
                 }
                 __syncwarp();
                 vector_item<VK>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn,
-                                S, va.out, k, T, (double *)buf);
+                                S, va.out, k, T, (double *)buf, true, kept);
             }
-        }
-        return;
-    }
-    const CtaTeam<8> T{(int)threadIdx.x, red};
-    // k_eig has finished with the stored-pair buffer: one slice per CTA here
-    double2 *buf = S.wbuf ? S.wbuf + (long long)blockIdx.x * S.wstride : nullptr;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) ticket = atomicAdd(S.cnt + C_WORK2, 1);
-        __syncthreads();
-        const int w = ticket;
-        if (w >= nfix) break;
-        const int k = S.fixlist[w];
-        fix_solve_item<K>(R, T, S, k, o, buf);
-        if (va.fused) {
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                place_item(S, k);
-                S.pos0[k] = S.pos[k];
-            }
-            __syncthreads();
-            vector_item<VK>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn, S,
-                            va.out, k, T, (double *)buf);
         }
     }
 }
@@ -230,7 +262,32 @@ __global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o, VecAr
 // ---------------------------------------------------------------------------
 // output placement and vectors
 // ---------------------------------------------------------------------------
-__global__ void k_place(Scratch S) { place_item(S, blockIdx.x * blockDim.x + threadIdx.x); }
+__global__ void k_place(Scratch S) {
+    const PartRange P = part_range(S);
+    const int ncomp = S.cnt[C_M] + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nk = P.k1 - P.k0;
+    if (i < nk) place_item(S, P.k0 + i);
+    else if (i < nk + P.u1 - P.u0) place_item(S, ncomp + P.u0 + (i - nk));
+}
+
+// One part of a split solve: its eigenpair range (an even split of the m + 1
+// computed eigenpairs), its deflated rows and its first output position.
+__global__ void k_part(Scratch S, int part, int nparts) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int nd = S.cnt[C_ND], ncomp = S.cnt[C_M] + 1;
+    const int k0 = (int)((long long)part * ncomp / nparts);
+    const int k1 = (int)((long long)(part + 1) * ncomp / nparts);
+    // deflated values (non-increasing) in [p_{k1-1}, p_{k0-1})
+    const int u0 = k0 == 0 ? 0 : count_ge(S.dval, nd, S.pv[k0 - 1], false);
+    const int u1 = k1 == ncomp ? nd : (k1 == 0 ? 0 : count_ge(S.dval, nd, S.pv[k1 - 1], false));
+    S.cnt[C_K0] = k0;
+    S.cnt[C_K1] = k1;
+    S.cnt[C_U0] = u0;
+    S.cnt[C_U1] = u1 > u0 ? u1 : u0;
+    S.cnt[C_POS0] = k0 + u0;
+    S.cnt[C_PART] = 1;
+}
 
 // All columns, or with va.fused (k_eig and k_fix_solve wrote the computed
 // ones) only those whose final position differs from the one used then, and
@@ -243,11 +300,14 @@ __global__ void __launch_bounds__(256) k_vectors(VecArgs va, Scratch S) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int ncomp = S.cnt[C_M] + 1;
-    const int nitems = ncomp + S.cnt[C_ND];
+    const PartRange P = part_range(S);
+    const int nk = P.k1 - P.k0;
+    const int nitems = nk + P.u1 - P.u0;
     const WarpTeam T{lane};
     double *stage = (S.wbuf && va.fused) ? (double *)(S.wbuf + (long long)warp * S.wstride)
                                          : nullptr;
-    for (int item = warp; item < nitems; item += nwarps) {
+    for (int i = warp; i < nitems; i += nwarps) {
+        const int item = i < nk ? P.k0 + i : ncomp + P.u0 + (i - nk);
         const bool cols = !(va.fused && item < ncomp) || S.pos[item] != S.pos0[item];
         vector_item<K>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn, S, va.out,
                        item, T, stage, cols);
@@ -365,8 +425,16 @@ static void launch_pipeline(int n, Scratch S, const SolveOpts &so, const RunOpts
     k_eig<K, VK><<<grid, 256, 0, st>>>(S, so, va);
     if (ro.ev[2]) cudaEventRecord(ro.ev[2], st);
     if (ro.fixup) {
-        k_fix_decide<<<(n + 255) / 256, 256, 0, st>>>(K, S, ro.knu_max);
-        const int fgrid = n < grid ? n : grid;
+        k_fix_decide<<<(n + 255) / 256, 256, 0, st>>>(K, S, ro.knu_max, n);
+        // every CTA resident at once (the remedies are assigned statically)
+        static int fix_per_sm = 0;
+        if (!fix_per_sm) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fix_per_sm, k_fix_solve<K, VK>, 256, 0);
+            if (fix_per_sm <= 0) fix_per_sm = 1;
+        }
+        int fgrid = sms * fix_per_sm;
+        fgrid = fgrid < grid ? fgrid : grid;
+        fgrid = n < fgrid ? n : fgrid;
         k_fix_solve<K, VK><<<fgrid, 256, 0, st>>>(S, so, va);
     }
     if (ro.ev[3]) cudaEventRecord(ro.ev[3], st);
@@ -427,6 +495,36 @@ cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, dou
             launch_pipeline<KIND_ARROW, KIND_NSYM>(n, S, so, ro, va, st);
             break;
     }
+    if (ro.ev[4]) cudaEventRecord(ro.ev[4], st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_arrow_part(int n, const double *d, const double *z, double alpha, int part,
+                              int nparts, int cap, const Outputs &out, const RunOpts &ro,
+                              Scratch S, cudaStream_t st, int *pos0, int *count) {
+    const int n1 = n - 1;
+    cudaError_t e = cudaMemsetAsync(S.cnt, 0, sizeof(int) * C_COUNT, st);
+    if (!e) e = cudaMemsetAsync(S.cnt64, 0, sizeof(unsigned long long) * C64_COUNT, st);
+    if (e) return e;
+    if (ro.ev[0]) cudaEventRecord(ro.ev[0], st);
+    if (n1 > 0) {
+        const int g = (n1 + 255) / 256;
+        k_check<<<g, 256, 0, st>>>(KIND_ARROW, n1, d, z, nullptr, 1.0, S);
+        k_rank<<<g, 256, 0, st>>>(n1, d, S.cnt, S.perm);
+    }
+    k_reduce<<<1, 1024, 0, st>>>(n1, d, z, S.perm, S);
+    k_post<KIND_ARROW><<<1, 1024, 0, st>>>(n1, d, z, nullptr, alpha, 0.0, S);
+    k_part<<<1, 32, 0, st>>>(S, part, nparts);
+    int h[C_COUNT];
+    e = cudaMemcpyAsync(h, S.cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return e;
+    *pos0 = h[C_POS0];
+    *count = (h[C_K1] - h[C_K0]) + (h[C_U1] - h[C_U0]);
+    if (!out.lambda || *count > cap) return cudaSuccess;   // size query, or no room
+    const SolveOpts so{ro.max_iter, ro.precision, ro.finish, ro.bgate, ro.kb_max};
+    const VecArgs va{n, n1, d, z, z, nullptr, alpha, 1.0, out, (S.wbuf && out.V) ? 1 : 0};
+    launch_pipeline<KIND_ARROW, KIND_ARROW>(n, S, so, ro, va, st);
     if (ro.ev[4]) cudaEventRecord(ro.ev[4], st);
     return cudaGetLastError();
 }

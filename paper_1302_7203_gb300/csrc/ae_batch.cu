@@ -171,8 +171,10 @@ __device__ __forceinline__ void batch_unit(const BatchInst &B, long long unit_in
                 B.S.pos0[k] = B.S.pos[k];
             }
             T.sync();
+            // (the stored differences only for whole-warp teams: narrower ones
+            // would add a sync per step to the divergent teams of one warp)
             vector_item<KIND_ARROW>(B.n, B.n1, B.d, B.z, B.z, nullptr, *B.alpha, 1.0, B.S,
-                                    B.out, k, T, (double *)tb);
+                                    B.out, k, T, (double *)tb, true, W == 32);
         }
     };
     if constexpr (W == 32) {
@@ -183,7 +185,7 @@ __device__ __forceinline__ void batch_unit(const BatchInst &B, long long unit_in
     }
 }
 
-__global__ void __launch_bounds__(256) k_batch_eig(const BatchInst *__restrict__ I, int count,
+__global__ void __launch_bounds__(256, 3) k_batch_eig(const BatchInst *__restrict__ I, int count,
                                                    const long long *__restrict__ uoff,
                                                    BatchCtl *ctl, SolveOpts o, double2 *wbuf,
                                                    long long wstride) {
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(256) k_batch_fix_solve(const BatchInst *__rest
         const BatchInst &B = I[ik.x];
         const Scratch &S = B.S;
         const auto R = PolesOf<KIND_ARROW>::make(S, S.cnt[C_M]);
-        fix_solve_item<KIND_ARROW>(R, T, S, ik.y, o, buf);
+        const bool kept = fix_solve_item<KIND_ARROW>(R, T, S, ik.y, o, buf);
         __syncwarp();
         if (B.out.V && buf) {
             if (lane == 0) {
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(256) k_batch_fix_solve(const BatchInst *__rest
             }
             __syncwarp();
             vector_item<KIND_ARROW>(B.n, B.n1, B.d, B.z, B.z, nullptr, *B.alpha, 1.0, S, B.out,
-                                    ik.y, T, (double *)buf);
+                                    ik.y, T, (double *)buf, true, kept);
         }
         __syncwarp();
     }
@@ -554,6 +556,8 @@ static cudaError_t plan_info(const Plan &P, ae_info *info, cudaStream_t st) {
         info->n_ddb += c[C_DDB];
         info->n_mid64 += c[C_MID64];
         info->total_deriv += (long long)u[C64_DERIV];
+        info->n_f32_passes += (long long)u[C64_F32];
+        info->n_df_passes += (long long)u[C64_DF];
         if (c[C_MAXIT] > info->max_iter_used) info->max_iter_used = c[C_MAXIT];
         info->total_iter += (long long)u[C64_ITERS];
         info->fix_iter += (long long)u[C64_ITERS_FIX];

@@ -14,8 +14,8 @@ enum {
     C_ND = 1,         // number of deflated rows
     C_FLAGS = 2,      // CF_* bits from k_check
     C_WORK = 3,       // work ticket of k_eig
-    C_NFIX = 4,       // length of the remedy list
-    C_WORK2 = 5,      // work ticket of k_fix_solve
+    C_NFIX = 4,       // remedies listed from the front of the remedy list
+    C_NFIX2 = 5,      // remedies listed from the back of the remedy list
     C_NEARZERO = 6,
     C_OTHERPOLE = 7,
     C_DPR1 = 8,
@@ -24,10 +24,19 @@ enum {
     C_FP32FB = 11,
     C_DDB = 12,       // b recomputed in double-double under the Algorithm 5 gate
     C_MID64 = 13,     // FP32 midpoint tests that needed the FP64 pass
-    C_COUNT = 16
+    // one part of a split solve (arrow_eig_part); C_PART = 0: the whole problem
+    C_PART = 14,
+    C_K0 = 15,        // computed eigenpairs [k0, k1) of the reduced arrowhead
+    C_K1 = 16,
+    C_U0 = 17,        // deflated rows [u0, u1) (in sorted order)
+    C_U1 = 18,
+    C_POS0 = 19,      // output position of the part's first item
+    C_COUNT = 20
 };
 enum { C64_ITERS = 0, C64_MAXKB = 1, C64_MAXKNU = 2, C64_ITERS_FIX = 3, C64_DERIV = 4,
-       C64_COUNT = 5 };
+       C64_F32 = 5,     // O(n) passes in FP32 (midpoint tests, FP32 steps and brackets)
+       C64_DF = 6,      // O(n) passes in double-float (opening model steps)
+       C64_COUNT = 7 };
 
 // k_check flag bits
 enum { CF_UNSORTED = 1, CF_ZERO = 2, CF_BAD = 4, CF_ZEROPOLE = 8 };
@@ -130,7 +139,16 @@ inline cudaError_t launch_arrow(int n, const double *d, const double *z, double 
                                 cudaStream_t st) {
     return launch_solve(KIND_ARROW, n, d, z, alpha, 0.0, out, ro, S, st);
 }
+// One part of a split arrow_eig (see arrow_eig_part): the reduction, then
+// (after a synchronisation that returns the part's first output position and
+// item count) the pipeline on the part's items, unless out.lambda is null or
+// the count exceeds cap.
+cudaError_t launch_arrow_part(int n, const double *d, const double *z, double alpha, int part,
+                              int nparts, int cap, const Outputs &out, const RunOpts &ro,
+                              Scratch S, cudaStream_t st, int *pos0, int *count);
 cudaError_t launch_debug_rcp(int n, const double *x, double *y, cudaStream_t st);
+// FMA throughput of the FP64 and FP32 pipes (TFLOP/s), either pointer may be null
+cudaError_t probe_fma_rates(double *fp64_tflops, double *fp32_tflops, cudaStream_t st);
 // remember a CUDA error for ae_last_cuda_error()
 void record_cuda_error(cudaError_t e);
 

@@ -116,6 +116,8 @@ extern "C" int arrow_eig_noalloc(int n, const double *d, const double *z, double
     info->n_ddb = cnt[ae::C_DDB];
     info->n_mid64 = cnt[ae::C_MID64];
     info->total_deriv = (long long)c64[ae::C64_DERIV];
+    info->n_f32_passes = (long long)c64[ae::C64_F32];
+    info->n_df_passes = (long long)c64[ae::C64_DF];
     if (cnt[ae::C_FLAGS] & ae::CF_BAD) return AE_ERR_INPUT;
     if (cnt[ae::C_CAPPED]) return AE_ERR_NOCONV;
     return AE_OK;

@@ -317,6 +317,8 @@ __device__ __forceinline__ void record_stats(const Scratch &S, const EigResult &
     atomicAdd(S.cnt64 + C64_ITERS, (unsigned long long)r.iters);
     if (r.iters_d && !fix) atomicAdd(S.cnt64 + C64_DERIV, (unsigned long long)r.iters_d);
     if (fix) atomicAdd(S.cnt64 + C64_ITERS_FIX, (unsigned long long)r.iters);
+    if (r.f32p) atomicAdd(S.cnt64 + C64_F32, (unsigned long long)r.f32p);
+    if (r.dfp) atomicAdd(S.cnt64 + C64_DF, (unsigned long long)r.dfp);
     atomicMax(S.cnt + C_MAXIT, r.iters);
     if (r.flags & AE_FLAG_CAPPED) atomicAdd(S.cnt + C_CAPPED, 1);
     if (r.flags & AE_FLAG_FP32_FALLBACK) atomicAdd(S.cnt + C_FP32FB, 1);
@@ -338,9 +340,11 @@ __device__ __forceinline__ void eig_item(const typename PolesOf<K>::type &R, con
         res = {a, S.prm[P_ALPHA_LO], a, NAN, 0.0, -1, 0, 0};
     } else {
         int i, side;
-        const bool mid64 = select_shift(R, T, k, i, side, o.precision == 1);
+        bool ran32 = false;
+        const bool mid64 = select_shift(R, T, k, i, side, o.precision == 1, &ran32);
         res = solve_shifted(R, T, i, side, o, buf);
         if (mid64) res.flags |= AE_FLAG_MID64;
+        if (ran32) ++res.f32p;
     }
     if (T.rank == 0) {
         store_result(S, k, res);
@@ -421,8 +425,9 @@ static __device__ int fix_decide_item(Kind kind, const Scratch &S, int k, double
 // Remedy solve of eigenpair k by a team (a CTA in the single-instance pipeline,
 // a warp in the batched one); all of its threads call it.
 // buf: the team's slice of stored pairs (or null).
+// Returns whether the remedy's result was kept (buf then holds its stored pairs).
 template <Kind K, class Team>
-__device__ void fix_solve_item(const typename PolesOf<K>::type &R, const Team &T, const Scratch &S,
+__device__ bool fix_solve_item(const typename PolesOf<K>::type &R, const Team &T, const Scratch &S,
                                int k, const SolveOpts &o, double2 *buf = nullptr) {
     const int m = S.cnt[C_M];
     const int f = S.es_flags[k];
@@ -452,6 +457,20 @@ __device__ void fix_solve_item(const typename PolesOf<K>::type &R, const Team &T
             S.es_flags[k] = f & ~(AE_FLAG_NEARZERO | AE_FLAG_OTHERPOLE | AE_FLAG_DPR1SHIFT);
         }
     }
+    return ok;
+}
+
+// The items a solve writes: all of them, or one part of a split solve --
+// computed eigenpairs [k0, k1) and the deflated rows [u0, u1) whose values
+// lie in [p_{k1-1}, p_{k0-1}), which together hold the output positions
+// [pos0, pos0 + (k1 - k0) + (u1 - u0)) of the whole decomposition.
+struct PartRange {
+    int k0, k1, u0, u1, pos0;
+};
+
+__device__ __forceinline__ PartRange part_range(const Scratch &S) {
+    if (!S.cnt[C_PART]) return {0, S.cnt[C_M] + 1, 0, S.cnt[C_ND], 0};
+    return {S.cnt[C_K0], S.cnt[C_K1], S.cnt[C_U0], S.cnt[C_U1], S.cnt[C_POS0]};
 }
 
 // number of entries of a non-increasing array that are >= x (or > x)
@@ -466,7 +485,10 @@ __device__ __forceinline__ int count_ge(const double *a, int len, double x, bool
     return lo;
 }
 
-// output position of item t (computed eigenpairs first, then deflated rows)
+// output position of item t (computed eigenpairs first, then deflated rows).
+// A deflated row's value v lies in its part's interval [p_{k1-1}, p_{k0-1}),
+// so every computed eigenvalue before k0 exceeds it and none from k1 on does:
+// only the part's own eigenvalues need comparing.
 static __device__ void place_item(const Scratch &S, int t) {
     const int m = S.cnt[C_M], nd = S.cnt[C_ND];
     const int ncomp = m + 1;
@@ -474,7 +496,8 @@ static __device__ void place_item(const Scratch &S, int t) {
         S.pos[t] = nd ? t + count_ge(S.dval, nd, S.es_lam[t], false) : t;
     } else if (t < ncomp + nd) {
         const int u = t - ncomp;
-        S.pos[t] = u + count_ge(S.es_lam, ncomp, S.dval[u], true);
+        const PartRange P = part_range(S);
+        S.pos[t] = u + P.k0 + count_ge(S.es_lam + P.k0, P.k1 - P.k0, S.dval[u], true);
     }
 }
 
@@ -508,13 +531,15 @@ __device__ __forceinline__ void run_column(const Scratch &S, const double *spk, 
 // stage: null (pass 1 keeps its values in the output column) or the team's
 // scratch for RS * n1 doubles (the column is then written once, normalised --
 // what an output in host memory needs).  columns = false writes the scalar
-// outputs only.
+// outputs only.  pairs: stage is the team's stored-pair slice and still holds
+// the (delta_j, zeta_j^2 / delta_j) of this item's final solve.
 template <Kind K, class Team>
 __device__ void vector_item(int n, int n1, const double *__restrict__ key,
                             const double *__restrict__ spk, const double *__restrict__ z,
                             const double *__restrict__ zrow, double alpha, double sgn,
                             const Scratch &S, const Outputs &out, int item, const Team &T,
-                            double *stage = nullptr, bool columns = true) {
+                            double *stage = nullptr, bool columns = true,
+                            bool pairs = false) {
     const int lane = T.rank;
     constexpr bool CPLX = K == KIND_HERM;
     constexpr bool TWO = K == KIND_NSYM;
@@ -522,7 +547,7 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
     const int m = S.cnt[C_M];
     const int ncomp = m + 1;
     const bool last_row = K != KIND_DPR1;     // arrowhead rows have the x_n = -1 entry
-    int pos = S.pos[item];
+    int pos = S.pos[item] - (S.cnt[C_PART] ? S.cnt[C_POS0] : 0);   // in this part's block
     if (K == KIND_DPR1 && sgn < 0.0) pos = n - 1 - pos;   // -M's order reversed
     double *col = (out.V && columns) ? out.V + (size_t)pos * out.ldv : nullptr;
     double *ucol = ((K == KIND_TSVD || TWO) && out.U && columns) ? out.U + (size_t)pos * out.ldu
@@ -596,12 +621,38 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
             }
         };
         double s = 0.0, s1 = 0.0;
-        int q0 = lane;
-        for (; q0 + Team::size < n1; q0 += 2 * Team::size) {
-            one(S.perm[q0], s);
-            one(S.perm[q0 + Team::size], s1);
+        // Sorted input without deflation: row r is reduced pole r, and its
+        // shifted difference d_r - sigma is the one the solve stored (0 for
+        // the shift pole): the same double, loaded instead of recomputed.  The
+        // staged values overwrite the stored pairs of rows up to r (a slot per
+        // row, 2 per pair; the complex stage overwrites row r's own), so each
+        // step's loads come before the team syncs and its stores after.
+        const bool fast = pairs && stage && (K == KIND_ARROW || CPLX || TWO) && m == n1 &&
+                          !(S.cnt[C_FLAGS] & CF_UNSORTED);
+        if (fast) {
+            const double2 *P = reinterpret_cast<const double2 *>(stage);
+            auto one_d = [&](int r, double del, double &acc) {
+                const double t = rcp(del - mu);
+                const double x = spk[r] * t;
+                keep[RS * r] = (CPLX || TWO) ? t : x;
+                acc = fma(x, x, acc);
+            };
+            for (int base = 0; base < n1; base += 2 * Team::size) {
+                const int ra = base + lane, rb = ra + Team::size;
+                const double da = ra < n1 ? P[ra].x : 0.0;
+                const double db = rb < n1 ? P[rb].x : 0.0;
+                T.sync();
+                if (ra < n1) one_d(ra, da, s);
+                if (rb < n1) one_d(rb, db, s1);
+            }
+        } else {
+            int q0 = lane;
+            for (; q0 + Team::size < n1; q0 += 2 * Team::size) {
+                one(S.perm[q0], s);
+                one(S.perm[q0 + Team::size], s1);
+            }
+            if (q0 < n1) one(S.perm[q0], s);
         }
-        if (q0 < n1) one(S.perm[q0], s);
         s += s1;
         s = T.sum(s) + (last_row ? 1.0 : 0.0);
         double inv, scale = 1.0;

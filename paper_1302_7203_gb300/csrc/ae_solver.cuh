@@ -49,7 +49,9 @@ struct EigResult {
     int pole;       // reduced pole index of the shift, -1 if none
     int iters;      // FP64 evaluations (bisection steps or Newton evaluations)
     int flags;
-    int iters_d;    // of those, Newton evaluations that also formed F' 
+    int iters_d;    // of those, Newton evaluations that also formed F'
+    int f32p;       // O(n) passes in FP32 (midpoint test, model steps, bracket)
+    int dfp;        // O(n) passes in double-float (model steps)
 };
 
 // ---------------------------------------------------------------------------
@@ -70,17 +72,24 @@ struct WarpTeam {
     __device__ __forceinline__ void sync() const { __syncwarp(); }
 };
 
-// A CTA of NW warps; `red` points at 2*NW doubles of shared memory.
+// NW consecutive warps of a CTA (the whole CTA when NW warps are all of it);
+// `red` points at 2*NW doubles of shared memory of this team alone, and the
+// team synchronises on its own named barrier `bar` (0: the CTA's barrier,
+// which then must be the whole CTA), so several teams can share a CTA.
 template <int NW>
 struct CtaTeam {
-    int rank;                       // threadIdx.x
+    int rank;                       // thread index within the team
     double *red;
+    int bar = 0;
     static constexpr int size = 32 * NW;
+    __device__ __forceinline__ void bsync() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(size) : "memory");
+    }
     __device__ __forceinline__ double sum(double v) const {
         v = warp_sum(v);
-        __syncthreads();
+        bsync();
         if ((rank & 31) == 0) red[rank >> 5] = v;
-        __syncthreads();
+        bsync();
         double r = red[0];
 #pragma unroll
         for (int w = 1; w < NW; ++w) r += red[w];
@@ -90,12 +99,12 @@ struct CtaTeam {
     __device__ __forceinline__ float sumf(float v) const { return (float)sum((double)v); }
     __device__ __forceinline__ dd sum(dd v) const {
         v = warp_sum_dd(v);
-        __syncthreads();
+        bsync();
         if ((rank & 31) == 0) {
             red[rank >> 5] = v.hi;
             red[NW + (rank >> 5)] = v.lo;
         }
-        __syncthreads();
+        bsync();
         dd r = {red[0], red[NW]};
 #pragma unroll
         for (int w = 1; w < NW; ++w) r = dd_add(r, dd{red[w], red[NW + w]});
@@ -103,9 +112,9 @@ struct CtaTeam {
     }
     __device__ __forceinline__ double max(double v) const {
         v = warp_max(v);
-        __syncthreads();
+        bsync();
         if ((rank & 31) == 0) red[rank >> 5] = v;
-        __syncthreads();
+        bsync();
         double r = red[0];
 #pragma unroll
         for (int w = 1; w < NW; ++w) r = fmax(r, red[w]);
@@ -113,15 +122,15 @@ struct CtaTeam {
     }
     __device__ __forceinline__ double min(double v) const {
         v = warp_min(v);
-        __syncthreads();
+        bsync();
         if ((rank & 31) == 0) red[rank >> 5] = v;
-        __syncthreads();
+        bsync();
         double r = red[0];
 #pragma unroll
         for (int w = 1; w < NW; ++w) r = fmin(r, red[w]);
         return r;
     }
-    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ void sync() const { bsync(); }
 };
 
 // ---------------------------------------------------------------------------
@@ -510,7 +519,8 @@ __device__ __forceinline__ float2 secular_sum_f32_d(const P &R, const Team &T, f
 // the same scale, far below the slack the margin keeps for it.
 template <class P, class Team>
 __device__ __forceinline__ bool select_shift(const P &R, const Team &T, int k, int &i,
-                                             int &side, bool f32 = false) {
+                                             int &side, bool f32 = false,
+                                             bool *ran32 = nullptr) {
     const int m = R.m;
     if (k == 0) {
         i = 0; side = +1;
@@ -527,6 +537,7 @@ __device__ __forceinline__ bool select_shift(const P &R, const Team &T, int k, i
     const double L = (double)((m + Team::size - 1) / Team::size);
     int sgn = 0;
     if (f32 && R.has_f32() && L < 0x1p16) {
+        if (ran32) *ran32 = true;
         float sh, sl;
         R.f32_shift(sk, k, sh, sl);
         const double sc = R.f32_scale();
@@ -733,7 +744,8 @@ __device__ __forceinline__ void quad_roots(double B, double P, double Wq, double
 // The new ends are NOT verified here.
 template <class P, class Team, class G64>
 __device__ bool fp32_narrow(const P &R, const Team &T, double shift, int skip, double K_over_s,
-                            int dir, G64 g64, double left, double right, double &l, double &r) {
+                            int dir, G64 g64, double left, double right, double &l, double &r,
+                            int &passes) {
     l = left;
     r = right;
     const double big = fmax(fabs(left), fabs(right));
@@ -753,6 +765,7 @@ __device__ bool fp32_narrow(const P &R, const Team &T, double shift, int skip, d
         const double x = s * (double)y;                 // the point actually evaluated
         if (!(x > l && x < r)) break;
         const float Tf = secular_sum_f32(R, T, sh, sl, sc, skip, y);
+        ++passes;
         const double KT = K * (double)Tf;
         const double phi = g64(x) - KT;
         if (!(fabs(phi) > 0x1p-24 * fabs(KT))) break;   // below FP32 resolution
@@ -985,6 +998,8 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                                    const SolveOpts &o, double2 *buf = nullptr) {
     EigResult res;
     res.flags = 0;
+    res.f32p = 0;
+    res.dfp = 0;
     const double sigma = R.pole(i);
     const double zi = R.zabs(i);
     const double wz = 1.0 / zi;         // w_zeta
@@ -1108,6 +1123,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                     const float y = (float)(x / s);
                     const double xe = s * (double)y;
                     const float2 Tf = secular_sum_f32_d(R, T, sh, sl, sc, i, y);
+                    ++res.f32p;
                     const double rx = rcp(xe);
                     const double F = (b - xe) + c * rx - K * (double)Tf.x;
                     const double dF = -1.0 - c * rx * rx - K * (double)Tf.y / s;
@@ -1148,6 +1164,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
             bool ok;
             const double2 Sd =
                 secular_sum_df_stored(buf, R.m, T, x0, ilogb(x0), ilogb(A.cabs), ok);
+            ++res.dfp;
             if (ok) {
                 const double rx = rcp(x0);
                 const double F = (b - x0) - c * (Sd.x - rx);
@@ -1183,7 +1200,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
         }
         if (f32) {
             double l, r;
-            if (!fp32_narrow(R, T, sigma, i, c, +1, G, left, right, l, r) ||
+            if (!fp32_narrow(R, T, sigma, i, c, +1, G, left, right, l, r, res.f32p) ||
                 !fp32_verify(+1, F64, l, r, left, right))
                 res.flags |= 64;
         }
@@ -1223,6 +1240,9 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
     res.pole = -1;
     res.b = NAN;
     res.flags = 0;
+    res.f32p = 0;
+    res.dfp = 0;
+    res.iters_d = 0;
     // q = number of poles above the shift: delta_j > 0 exactly for j < q, so
     // the largest 1/delta_j is 1/delta_{q-1} and the smallest 1/delta_q (the
     // poles are sorted and the shift is none of them)
@@ -1305,6 +1325,7 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
             for (int t = 0; t < 3 && x != 0.0 && isfinite(x); ++t) {
                 bool ok;
                 const double2 Sd = secular_sum_df_stored(buf, R.m, T, x, ilogb(x), kc, ok);
+                ++res.dfp;
                 if (!ok) break;
                 const double rx = rcp(x);
                 const double F = sg * fma(rho, Sd.x - rx, 1.0);

@@ -1,6 +1,8 @@
 """Host-side pieces of bench.py (no GPU): the algorithmic flop count behind
 roofline.achieved, the forms table, the clock-sample summary and the
 workload description."""
+import numpy as np
+
 import bench
 
 
@@ -65,3 +67,61 @@ def test_workload_config():
     assert c["n"] == 16384 and c["form"] == "fp32_newton_gated"
     assert c["parallelism"] == "2 independent instances"
     assert "16384" in c["workload"]
+
+
+def test_fp64_instruction_model():
+    info = {"n_reduced": 100, "total_iter": 130, "fix_iter": 10, "n_ddb": 7,
+            "total_deriv": 20, "n_mid64": 3}
+    n = 101
+    c = bench.INSTR_PER_TERM
+    got = bench.fp64_instructions(n, info, "fp32_newton_gated")
+    per_terms = (c["mid"] * 3 + c["b_std"] * 100 + c["b_dd"] * 7 + c["eval"] * 120 +
+                 c["deriv"] * 20)
+    assert got == (n - 2) * per_terms + c["vector"] * 100 * (n - 1)
+    # without the gate every b is double-double; in FP64 every midpoint test runs
+    got = bench.fp64_instructions(n, info, "fp64_newton")
+    per_terms = c["mid"] * 100 + c["b_dd"] * 100 + c["eval"] * 120 + c["deriv"] * 20
+    assert got == (n - 2) * per_terms + c["vector"] * 100 * (n - 1)
+
+
+def test_fp32_flops_and_roofline_numbers():
+    info = {"n_f32_passes": 10, "n_df_passes": 4}
+    f = bench.FP32_FLOPS_PER_TERM
+    assert bench.fp32_flops(52, info) == 50 * (f["f32"] * 10 + f["df"] * 4)
+    peaks = {"fp64_tflops": 1.0, "fp32_tflops": 64.0}
+    r = bench.roofline_numbers(0.5e12, 0.25e12, 16e12, 1.0, peaks)
+    assert r["achieved"] == 0.5 and r["frac"] == 0.5
+    # 0.25e12 FMA lane-instructions at 0.5e12 a second: half the pipe's time
+    assert r["fp64_pipe_busy_implied"] == 0.5
+    # FP32 needs 0.25 s, FP64 0.5 s: the FP64 pipe bounds
+    assert r["mixed"]["frac"] == 0.5 and r["mixed"]["t_fp32_ms"] == 250.0
+
+
+def test_batch_terms_weights_by_eigenpairs():
+    assert bench.batch_terms([10]) == 8.0
+    # 10 eigenpairs of 8 terms and 30 of 28 terms
+    assert bench.batch_terms([10, 30]) == (10 * 8 + 30 * 28) / 40
+
+
+def test_reference_arm_keeps_every_core_busy():
+    for t in (1, 8, 16):
+        assert bench.reference_per_step(t) >= 4 * t
+
+
+def test_error_summary_and_parity_flag():
+    n = 100
+    res = {"lam": np.array([1.0, -2.0, 0.0]), "abserr": np.array([0.0, 0.0, 1e-30]),
+           "V": np.eye(3)}
+    e = bench.max_err_neps(np.array([1.0, -2.0 * (1 + 5 * n * bench.EPS64), 0.0]),
+                           np.eye(3), res, n)
+    assert abs(e["lambda"] - 5.0) < 1e-9 and e["vectors"] == 0.0
+    # the exact zero is compared against the oracle's bound (counted as widened)
+    assert e["widened"] == 1 and e["pairs"] == 3
+    assert bench.err_ok(e) and bench.err_ok(None)
+    e["vectors"] = 10.5
+    assert not bench.err_ok(e)
+
+
+def test_sample_positions():
+    ks = bench.sample_ks(1000, 64)
+    assert ks[0] == 0 and ks[-1] == 999 and 500 in ks and np.all(np.diff(ks) > 0)

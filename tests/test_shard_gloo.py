@@ -85,3 +85,138 @@ def test_two_ranks_solve_a_packed_batch(tmp_path):
         ref = oracle.arrow_eig(d, z, a, nthreads=1)
         np.testing.assert_array_equal(data[f"l{i}"], ref["lam"])
         np.testing.assert_array_equal(data[f"v{i}"], ref["V"])
+
+
+# ----------------------------------------------------------------------------
+# one instance split by eigenpair ranges
+# ----------------------------------------------------------------------------
+def _reduced(d, z):
+    """Reduced poles and deflated values (sorted order) from the oracle's reduction."""
+    import oracle
+    order, kind, head, m = oracle.reduce(d, z)
+    poles = np.array([d[r] for r in order if kind[r] == 0])
+    defl = np.array([d[r] for r in order if kind[r] != 0])
+    assert poles.size == m
+    return poles, defl
+
+
+def _deflating_instance(n=61, seed=3):
+    d, z, a = W.uniform_arrow(n, seed=seed)
+    d = d.copy()
+    z = z.copy()
+    z[[4, 20, 21]] = 0.0                   # zero spikes
+    d[[9, 10]] = d[8]                      # a run of three equal poles
+    d[[30, 31]] = d[29]
+    z[31] = 0.0                            # a zero spike inside a run
+    return d, z, a
+
+
+@pytest.mark.parametrize("nparts", [1, 2, 3, 5, 8])
+def test_part_items_cover_the_output_in_order(nparts):
+    import oracle
+    for d, z, a in (_deflating_instance(), W.uniform_arrow(40, seed=1)):
+        n = len(d) + 1
+        poles, defl = _reduced(d, z)
+        ref = oracle.arrow_eig(d, z, a, vectors=False)["lam"]
+        nxt = 0
+        for p in range(nparts):
+            k0, k1, u0, u1, pos0, cnt = shard.part_items(poles, defl, p, nparts)
+            assert pos0 == nxt                 # contiguous, in part order
+            nxt += cnt
+            hi = np.inf if k0 == 0 else poles[k0 - 1]
+            lo = -np.inf if k1 == poles.size + 1 else (np.inf if k1 == 0 else poles[k1 - 1])
+            block = ref[pos0:pos0 + cnt]
+            # the part's items are exactly the values in [p_{k1-1}, p_{k0-1})
+            assert np.all(block < hi) and np.all(block >= lo)
+            assert cnt == (k1 - k0) + (u1 - u0)
+        assert nxt == n
+    with pytest.raises(ValueError):
+        shard.part_bounds(10, 2, 2)
+
+
+def _split_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        out = {}
+        # (1) an instance with deflation: each rank solves its block with the
+        # oracle; rank 0 merges the blocks
+        d, z, a = _deflating_instance()
+        n = len(d) + 1
+        poles, defl = _reduced(d, z)
+        _, _, _, _, pos0, cnt = shard.part_items(poles, defl, rank, world)
+        ks = np.arange(pos0, pos0 + cnt)
+        r = oracle.arrow_eig(d, z, a, ks=ks, nthreads=1) if cnt else {"lam": np.zeros(0),
+                                                                       "V": np.zeros((n, 0))}
+        got = shard.gather_to_root((pos0, r["lam"], r["V"]))
+        if rank == 0:
+            out["lam"], out["V"] = shard.merge_parts(n, got)
+        # (2) the one-eigenpair halo on an instance without deflation: each rank
+        # recomputes the eigenvalue just outside each end of its range; the
+        # edge values every rank owns are gathered and must match bit for bit
+        d2, z2, a2 = W.graded_arrow(97, seed=5)
+        n2 = len(d2) + 1
+        k0, k1 = shard.part_bounds(n2, rank, world)
+        halo = [k for k in (k0 - 1, k1) if 0 <= k < n2]
+        mine = oracle.arrow_eig(d2, z2, a2, ks=np.arange(k0, k1), vectors=False, nthreads=1)
+        hal = oracle.arrow_eig(d2, z2, a2, ks=np.array(halo), vectors=False, nthreads=1)
+        edges = shard.gather_to_root(({k0: mine["lam"][0], k1 - 1: mine["lam"][-1]},
+                                      dict(zip(halo, hal["lam"]))))
+        if rank == 0:
+            owned = {}
+            for e, _ in edges:
+                owned.update(e)
+            out["halo_ok"] = all(owned[k] == v for _, h in edges for k, v in h.items())
+            out["halo_count"] = sum(len(h) for _, h in edges)
+            np.savez(out_path, **out)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_instance_merges_to_the_whole(tmp_path, world):
+    import oracle
+    oracle.threads()
+    path = str(tmp_path / "split.npz")
+    mp.start_processes(_split_worker, args=(world, _free_port(), path), nprocs=world,
+                       join=True, start_method="spawn")
+    data = np.load(path)
+    d, z, a = _deflating_instance()
+    ref = oracle.arrow_eig(d, z, a, nthreads=1)
+    np.testing.assert_array_equal(data["lam"], ref["lam"])
+    np.testing.assert_array_equal(data["V"], ref["V"])
+    assert bool(data["halo_ok"]) and int(data["halo_count"]) == 2 * (world - 1)
+
+
+def _leaving_worker(rank, world, port, out_path):
+    from datetime import timedelta
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0, timedelta(seconds=30))
+    import oracle
+    d, z, a = W.uniform_arrow(30, seed=rank)
+    oracle.arrow_eig(d, z, a, nthreads=1)            # step 0
+    shard.arrive(store, 0, rank)
+    if rank == world - 1:
+        return                                       # leaves between steps
+    missing0 = shard.missing_ranks(store, 0, world, timeout_s=10.0)
+    shard.arrive(store, 1, rank)                     # done with step 1's host part
+    missing1 = shard.missing_ranks(store, 1, world, timeout_s=1.0)
+    with open(f"{out_path}.{rank}", "w") as f:
+        f.write(f"{missing0} {missing1}")
+    store.set(f"done/{rank}", "1")
+    if rank == 0:                                    # keep the store up for the others
+        store.wait([f"done/{r}" for r in range(world - 1)])
+
+
+def test_a_rank_that_leaves_between_steps_is_reported(tmp_path):
+    import oracle
+    oracle.threads()
+    path = str(tmp_path / "gone")
+    world = 3
+    mp.start_processes(_leaving_worker, args=(world, _free_port(), path), nprocs=world,
+                       join=True, start_method="spawn")
+    for r in range(world - 1):
+        with open(f"{path}.{r}") as f:
+            assert f.read() == "[] [2]"
