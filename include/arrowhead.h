@@ -485,8 +485,13 @@ int arrow_eig_host(int n, const double *d_host, const double *z_host, double alp
  * returns AE_ERR_TOO_LARGE without touching the GPU).  The call issues no
  * cudaMalloc/cudaFree and no allocating library routine.
  *  - Its first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress, with that device current) and, with CUDA's
+ *    default lazy module loading, is when the array and the solver's kernels
+ *    are loaded onto that device, which takes device memory.  So make one
+ *    call on each device (an n = 1 call will do) before reserving the rest of
+ *    the device's memory and before any stream capture; later calls take none.
+ *  - The looked-up address is kept for the life of the process: after a
+ *    cudaDeviceReset the entry point must not be called again on that device.
  *  - All calls on a device share the one array: calls that may overlap on the
  *    GPU (different streams, or different host threads) race and corrupt each
  *    other's results.  Serialise them, e.g. on one stream.

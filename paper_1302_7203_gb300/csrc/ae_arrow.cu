@@ -139,17 +139,18 @@ __global__ void __launch_bounds__(256, 3) k_eig(Scratch S, SolveOpts o, VecArgs 
     double2 *buf = S.wbuf ? S.wbuf + gw * S.wstride : nullptr;
     // a part also solves the eigenpair on each side of its range (Algorithm
     // 1's solve only, the same bits its owner computes): the remedy decision
-    // of Eq. (K0) needs both neighbours
-    const PartRange P = part_range(S);
-    const int k_lo = P.k0 > 0 ? P.k0 - 1 : 0;
-    const int k_hi = P.k1 <= m ? P.k1 + 1 : m + 1;
+    // of Eq. (K0) needs both neighbours.  Its tickets start at its first such
+    // eigenpair (k_part sets the counter); the range is re-read per item
+    // rather than held in registers across the solve.
+    const int k_hi = S.cnt[C_PART] ? S.cnt[C_KHI] : m + 1;
     for (;;) {
         int k = 0;
-        if (lane == 0) k = k_lo + atomicAdd(S.cnt + C_WORK, 1);
+        if (lane == 0) k = atomicAdd(S.cnt + C_WORK, 1);
         k = __shfl_sync(FULL, k, 0);
         if (k >= k_hi) break;
         eig_item<K>(R, T, S, k, o, buf);
-        if (va.fused && k >= P.k0 && k < P.k1) {
+        if (va.fused && (!__ldcg(S.cnt + C_PART) ||
+                         (k >= __ldcg(S.cnt + C_K0) && k < __ldcg(S.cnt + C_K1)))) {
             __syncwarp();
             if (lane == 0) {
                 place_item(S, k);
@@ -286,6 +287,8 @@ __global__ void k_part(Scratch S, int part, int nparts) {
     S.cnt[C_U0] = u0;
     S.cnt[C_U1] = u1 > u0 ? u1 : u0;
     S.cnt[C_POS0] = k0 + u0;
+    S.cnt[C_WORK] = k0 > 0 ? k0 - 1 : 0;             // k_eig's first ticket
+    S.cnt[C_KHI] = k1 < ncomp ? k1 + 1 : ncomp;
     S.cnt[C_PART] = 1;
 }
 

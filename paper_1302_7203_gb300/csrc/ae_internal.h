@@ -31,7 +31,8 @@ enum {
     C_U0 = 17,        // deflated rows [u0, u1) (in sorted order)
     C_U1 = 18,
     C_POS0 = 19,      // output position of the part's first item
-    C_COUNT = 20
+    C_KHI = 20,       // end of the eigenpairs k_eig solves (the part's range and its edges)
+    C_COUNT = 21
 };
 enum { C64_ITERS = 0, C64_MAXKB = 1, C64_MAXKNU = 2, C64_ITERS_FIX = 3, C64_DERIV = 4,
        C64_F32 = 5,     // O(n) passes in FP32 (midpoint tests, FP32 steps and brackets)

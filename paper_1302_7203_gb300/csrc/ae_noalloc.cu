@@ -7,7 +7,9 @@
 // where a cudaMalloc/cudaMallocAsync could block on the driver, fail under
 // memory pressure or fragment the reserved pool.  For them the O(n) scratch of
 // the solve lives in g_noalloc_scratch below: AE_NOALLOC_SCRATCH_BYTES bytes
-// that every GPU loading this library holds until the process exits.
+// that every GPU holds until the process exits once this code has been loaded
+// onto it -- with CUDA's lazy module loading, at the first call there, which
+// is why callers make one call per device before reserving its memory.
 //
 // Host code must not pass g_noalloc_scratch itself to a kernel: on the host
 // that name denotes a host-side shadow, not a device address.  The device

@@ -78,3 +78,84 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(ae):
                                     None)
     assert st == ae.AE_ERR_TOO_LARGE
     assert b"static scratch" in ae.lib().ae_status_string(st)
+
+
+def _cudart():
+    """The CUDA runtime (any copy: the memory pool queried is the device's)."""
+    import glob
+    import os
+    cands = ["libcudart.so.13", "libcudart.so"]
+    cands += glob.glob("/usr/local/cuda/lib64/libcudart.so*")
+    try:
+        import nvidia
+        for base in nvidia.__path__:
+            cands += glob.glob(os.path.join(base, "*", "lib", "libcudart.so*"))
+    except ImportError:
+        pass
+    for c in cands:
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    pytest.skip("no CUDA runtime library to query the memory pool with")
+
+
+def _pool_bytes(rt):
+    """(used, reserved) bytes of the current device's default memory pool,
+    which every cudaMallocAsync of this library draws from."""
+    dev = ctypes.c_int()
+    assert rt.cudaGetDevice(ctypes.byref(dev)) == 0
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    used, res = ctypes.c_uint64(), ctypes.c_uint64()
+    assert rt.cudaMemPoolGetAttribute(pool, 0x7, ctypes.byref(used)) == 0   # UsedMemCurrent
+    assert rt.cudaMemPoolGetAttribute(pool, 0x5, ctypes.byref(res)) == 0    # ReservedMemCurrent
+    return used.value, res.value
+
+
+def test_noalloc_allocates_nothing(ae):
+    # what the entry point exists for: after a first call on the device (which
+    # loads the library's kernels and looks up the array), a call changes
+    # neither the device's free memory nor its stream-ordered memory pool
+    from paper_1302_7203_gb300 import workloads as W
+    rt = _cudart()
+    d, z, alpha = W.graded_arrow(2000, seed=43)
+    _noalloc(ae, d, z, alpha)                       # warm-up call
+    n = len(d) + 1
+    dt = torch.as_tensor(d, device="cuda")
+    zt = torch.as_tensor(z, device="cuda")
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    V = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    pool0 = _pool_bytes(rt)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = ae.lib().arrow_eig_noalloc(n, ctypes.c_void_p(dt.data_ptr()),
+                                    ctypes.c_void_p(zt.data_ptr()), float(alpha),
+                                    ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                                    n, None, None, None, None, None, stream)
+    assert st == ae.AE_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert _pool_bytes(rt) == pool0
+
+
+def test_noalloc_accepts_its_largest_order(ae):
+    # n = 20928 is the largest order whose scratch fits the static array
+    from paper_1302_7203_gb300 import workloads as W
+    n = 20928
+    d, z, alpha = W.uniform_arrow(n, seed=44)
+    dt = torch.as_tensor(d, device="cuda")
+    zt = torch.as_tensor(z, device="cuda")
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    info = ae.AeInfo()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = ae.lib().arrow_eig_noalloc(n, ctypes.c_void_p(dt.data_ptr()),
+                                    ctypes.c_void_p(zt.data_ptr()), float(alpha),
+                                    ctypes.c_void_p(lam.data_ptr()), None, n, None, None, None,
+                                    ctypes.byref(info), None, stream)
+    assert st == ae.AE_OK, ae.lib().ae_status_string(st)
+    torch.cuda.synchronize()
+    lam = lam.cpu().numpy()
+    assert info.n_reduced == n and np.all(np.diff(lam) <= 0)
+    assert np.all(lam[:-1] >= d) and np.all(d >= lam[1:])   # interlacing (Sec. 1)
