@@ -659,13 +659,14 @@ def serve_sweep(arrowhead, W, dev, count, rates, opts):
         srv.close()
         res[f"{int(rate)}/s"] = {"offered_per_s": rate, "requests": m,
                                  "completed": st["completed"], "rejected": rejected,
-                                 "failed": st["failed"],
+                                 "failed": st["failed"], "merged": st["merged"],
                                  "goodput_per_s": st["completed"] / wall,
                                  "p50_ms": 1e3 * st["p50_s"], "p99_ms": 1e3 * st["p99_s"],
                                  "eigenpairs_per_s": st["eigenpairs_per_s"],
                                  "wall_s": wall}
     res["mix"] = ("arrow/DPR1/SVD uniform, orders log-uniform [64, 16384], vectors kept on "
-                  "device; the same requests at every rate")
+                  "device; the same requests at every rate; 16 streams; runs of arrowheads of "
+                  "order <= 1024 at the head of the queue merged into batched passes")
     res["max_err_neps"] = checked
     return res
 

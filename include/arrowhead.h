@@ -407,7 +407,13 @@ int ae_team_width(int n);
  * covers the request's scratch and results.  Admitted requests of any kind and
  * size run concurrently on their streams; results stay on the device, owned by
  * the server, until released.  Latency is submit -> observed completion.
- * The solves are those of arrow_eig / dpr1_eig / tri_arrow_svd.
+ * The solves are those of arrow_eig / dpr1_eig / tri_arrow_svd.  Arrowhead
+ * requests of order <= 1024 waiting among the first 1024 of the queue (up to
+ * 256, in queue order, all with or all without vectors) are admitted together,
+ * ahead of the larger requests between them: one pass of the batched stages
+ * (one 32-lane team per eigenpair) on one stream solves them all, each into
+ * its own result buffers; their results have the bits arrow_eig gives, except
+ * remedied eigenpairs (Remarks 1, 2), which agree within the tolerance.
  */
 #define AE_KIND_ARROW 0
 #define AE_KIND_DPR1 1
@@ -434,6 +440,7 @@ typedef struct ae_serve_stats_t {
     double p50_s, p99_s, max_s; /* latency percentiles of completed requests */
     double eigenpairs_per_s;    /* completed pairs / (last completion - first submit) */
     int cuda_error;             /* a CUDA error the worker met, else 0 */
+    long long merged;           /* requests admitted in merged batched passes */
 } ae_serve_stats_t;
 
 typedef struct ae_server ae_server;
@@ -505,8 +512,9 @@ int arrow_eig_noalloc(int n, const double *d, const double *z, double alpha,
  * ae_fma_peaks -- measured fused multiply-add throughput of this GPU's FP64
  * and FP32 pipes in TFLOP/s (2 flops per FMA), the denominators of the
  * solver's roofline.  The paper has no counterpart: it is a measurement aid.
- * A grid that fills every SM runs independent FMA chains (8 per thread);
- * each rate is the best of three CUDA-event-timed launches after a warm-up
+ * A grid that fills every SM runs independent FMA chains (8 per thread, all
+ * operands in registers); each rate is the best of three CUDA-event-timed
+ * launches after a warm-up
  * (about 0.1 s for FP64, 0.04 s for FP32) on `stream`, which the call
  * synchronises.  Either output pointer (host) may be NULL, not both (-1).
  */

@@ -79,7 +79,8 @@ class AeServeStats(ctypes.Structure):
                                                   "failed", "queued", "running")] + \
         [("bytes_in_use", ctypes.c_size_t), ("eigenpairs", ctypes.c_longlong),
          ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("max_s", ctypes.c_double),
-         ("eigenpairs_per_s", ctypes.c_double), ("cuda_error", ctypes.c_int)]
+         ("eigenpairs_per_s", ctypes.c_double), ("cuda_error", ctypes.c_int),
+         ("merged", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -513,6 +513,104 @@ static cudaError_t build_plan(Plan *P, int count, const long long *n_off, const 
     return cudaStreamSynchronize(st);
 }
 
+// ---------------------------------------------------------------------------
+// a batch of separate requests (the serving loop): instances with their own
+// input and output buffers, solved by one pass of the batched stages
+// ---------------------------------------------------------------------------
+// Layout of the one device block a request batch needs: descriptors, prefix
+// tables, remedy list, control block, corners, per-instance scratch and the
+// stored-pair slices; every part 256-byte aligned.
+struct ReqBatchLayout {
+    size_t inst, eoff, uoff, fix, ctl, alpha, scratch, wbuf, total;
+    long long wstride;
+    std::vector<size_t> soff;
+};
+
+static ReqBatchLayout req_batch_layout(int count, const int *ns) {
+    ReqBatchLayout L;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    long long total_n = 0, nmax = 1;
+    L.soff.assign(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+        total_n += ns[i];
+        nmax = std::max<long long>(nmax, ns[i]);
+        L.soff[i + 1] = L.soff[i] + up(arrow_scratch_bytes(ns[i]));
+    }
+    L.wstride = (nmax + 1) & ~1LL;
+    size_t p = 0;
+    L.inst = p; p += up(sizeof(BatchInst) * count);
+    L.eoff = p; p += up(sizeof(long long) * (count + 1));
+    L.uoff = p; p += up(sizeof(long long) * (count + 1));
+    L.fix = p;  p += up(sizeof(int2) * (size_t)(total_n > 0 ? total_n : 1));
+    L.ctl = p;  p += up(sizeof(BatchCtl));
+    L.alpha = p; p += up(sizeof(double) * count);
+    L.scratch = p; p += L.soff[count];
+    L.wbuf = p; p += sizeof(double2) * (size_t)L.wstride * 4 * (size_t)batch_eig_grid() * 8;
+    L.total = p + 256;
+    return L;
+}
+
+size_t req_batch_bytes(int count, const int *ns) { return req_batch_layout(count, ns).total; }
+
+// Solve `count` arrowhead requests (orders ns, inputs d[i], z[i] with corner
+// alpha[i], outputs lam[i] and V[i] with ld = n) with the batched stages on
+// `st`, using the device block `block` of req_batch_bytes() bytes.  Every
+// eigenpair is solved by a 32-lane team, so each result has the bits the
+// single-instance solve gives (remedies, solved by a warp here and by a team
+// as wide as one wave allows there, agree within the tolerance).  cnt[i]
+// receives the device address of instance i's counters (C_COUNT ints).
+cudaError_t launch_req_batch(int count, const int *ns, const double *const *d,
+                             const double *const *z, const double *alpha, double *const *lam,
+                             double *const *V, void *block, const RunOpts &ro, cudaStream_t st,
+                             const int **cnt) {
+    const ReqBatchLayout L = req_batch_layout(count, ns);
+    char *b = (char *)(((uintptr_t)block + 255) & ~(uintptr_t)255);
+    Plan P;
+    P.count = count;
+    P.ro = ro;
+    P.so = SolveOpts{ro.max_iter, ro.precision, ro.finish, ro.bgate, ro.kb_max};
+    P.d_inst = (BatchInst *)(b + L.inst);
+    P.d_eoff = (long long *)(b + L.eoff);
+    P.d_uoff = (long long *)(b + L.uoff);
+    P.d_fix = (int2 *)(b + L.fix);
+    P.d_ctl = (BatchCtl *)(b + L.ctl);
+    P.wbuf = (double2 *)(b + L.wbuf);
+    P.wstride = L.wstride;
+    double *d_alpha = (double *)(b + L.alpha);
+    std::vector<BatchInst> host(count);
+    std::vector<long long> eoff(count + 1, 0), uoff(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+        BatchInst &B = host[i];
+        B.n = ns[i];
+        B.n1 = ns[i] - 1;
+        B.d = d[i];
+        B.z = z[i];
+        B.alpha = d_alpha + i;
+        B.S = carve_scratch(b + L.scratch + L.soff[i], ns[i]);
+        B.out = Outputs{};
+        B.out.lambda = lam[i];
+        B.out.V = V ? V[i] : nullptr;
+        B.out.ldv = ns[i];
+        B.team = 32;
+        eoff[i + 1] = eoff[i] + ns[i];
+        uoff[i + 1] = uoff[i] + ns[i];
+        cnt[i] = B.S.cnt;
+    }
+    P.total_n = eoff[count];
+    // (pageable sources: each copy is staged before the call returns)
+    cudaError_t e = cudaMemcpyAsync(P.d_inst, host.data(), sizeof(BatchInst) * count,
+                                    cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(P.d_eoff, eoff.data(), sizeof(long long) * (count + 1),
+                                cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(P.d_uoff, uoff.data(), sizeof(long long) * (count + 1),
+                                cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(d_alpha, alpha, sizeof(double) * count, cudaMemcpyHostToDevice,
+                                st);
+    if (e) return e;
+    enqueue(P, st);
+    return cudaGetLastError();
+}
+
 static cudaError_t capture_plan(Plan *P) {
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);

@@ -148,6 +148,13 @@ cudaError_t launch_arrow_part(int n, const double *d, const double *z, double al
                               int nparts, int cap, const Outputs &out, const RunOpts &ro,
                               Scratch S, cudaStream_t st, int *pos0, int *count);
 cudaError_t launch_debug_rcp(int n, const double *x, double *y, cudaStream_t st);
+// Requests of the serving loop solved together by the batched stages (see
+// ae_batch.cu): the device block they need, and the launch.
+size_t req_batch_bytes(int count, const int *ns);
+cudaError_t launch_req_batch(int count, const int *ns, const double *const *d,
+                             const double *const *z, const double *alpha, double *const *lam,
+                             double *const *V, void *block, const RunOpts &ro, cudaStream_t st,
+                             const int **cnt);
 // FMA throughput of the FP64 and FP32 pipes (TFLOP/s), either pointer may be null
 cudaError_t probe_fma_rates(double *fp64_tflops, double *fp32_tflops, cudaStream_t st);
 // remember a CUDA error for ae_last_cuda_error()

@@ -631,8 +631,9 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
                           !(S.cnt[C_FLAGS] & CF_UNSORTED);
         if (fast) {
             const double2 *P = reinterpret_cast<const double2 *>(stage);
+            const double one = unit_reg();
             auto one_d = [&](int r, double del, double &acc) {
-                const double t = rcp(del - mu);
+                const double t = rcp_o(del - mu, one);
                 const double x = spk[r] * t;
                 keep[RS * r] = (CPLX || TWO) ? t : x;
                 acc = fma(x, x, acc);

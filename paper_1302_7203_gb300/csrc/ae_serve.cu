@@ -10,7 +10,14 @@
 //      (results stay on the device, owned by the server, until released).
 // An admitted request runs the same pipeline as arrow_eig / dpr1_eig /
 // tri_arrow_svd on its slot's stream, so requests admitted while others run
-// overlap on the GPU.  Nothing on the device waits for the host.
+// overlap on the GPU.  Small arrowhead requests waiting among the first
+// kScan of the queue (order at most kSmallN, up to kMergeMax of them, in
+// their queue order, ahead of the larger requests between them) are admitted
+// as one: a single pass of the batched stages on one slot solves them all,
+// one 32-lane team per eigenpair, so that their results carry the
+// single-instance solve's bits (remedied eigenpairs agree within the
+// tolerance), while each keeps its own result buffers and completion.
+// Nothing on the device waits for the host.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -52,6 +59,14 @@ size_t wbuf_bytes(int n) {
     return sizeof(double2) * (size_t)((n + 1) & ~1) * (size_t)ae::eig_grid_warps(n);
 }
 
+constexpr int kSmallN = 1024;     // orders merged into one batched pass
+constexpr int kMergeMax = 256;    // requests per merged pass
+constexpr int kScan = 1024;       // queue entries searched for them
+
+bool mergeable(const ae_request &r) {
+    return r.kind == AE_KIND_ARROW && r.n >= 2 && r.n <= kSmallN;
+}
+
 size_t result_doubles(const ae_request &r) {
     const size_t n = (size_t)r.n;
     size_t k = n;                                          // eigen/singular values
@@ -84,10 +99,109 @@ struct ae_server {
     clk::time_point t_first, t_last;
     int worker_error = cudaSuccess;
 
+    long long merged = 0;             // requests solved in merged batched passes
+
     void loop();
     bool admit_locked(Req *r);
+    int admit_merged_locked();
     void retire_locked(Req *r);
 };
+
+// Admit the small arrowhead requests among the first kScan of the queue (all
+// with the want_vectors of the first of them) as one batched pass on one free
+// slot; returns how many were admitted (0: fewer than two waiting, or no slot
+// or memory now).
+int ae_server::admit_merged_locked() {
+    std::vector<int> at;              // their queue positions, in order
+    int want = -1;
+    for (int q = 0; q < (int)queue.size() && q < kScan && (int)at.size() < kMergeMax; ++q) {
+        const ae_request &r = queue[q]->in;
+        if (!mergeable(r) || (want >= 0 && r.want_vectors != want)) continue;
+        want = r.want_vectors;
+        at.push_back(q);
+    }
+    const int cnt = (int)at.size();
+    if (cnt < 2) return 0;
+    int slot = -1;
+    for (int s = 0; s < max_inflight; ++s)
+        if (!slot_busy[s]) { slot = s; break; }
+    if (slot < 0) return 0;
+    std::vector<int> ns(cnt);
+    std::vector<Req *> rs(cnt);
+    size_t res_bytes = 0;
+    for (int i = 0; i < cnt; ++i) {
+        rs[i] = queue[at[i]];
+        ns[i] = rs[i]->in.n;
+        res_bytes += sizeof(double) * result_doubles(rs[i]->in);
+    }
+    const size_t block_bytes = ae::req_batch_bytes(cnt, ns.data());
+    if (in_use + res_bytes + block_bytes > budget && !(inflight.empty() && in_use == 0))
+        return 0;
+    cudaStream_t st = streams[slot];
+    void *block = nullptr;
+    cudaError_t e = cudaMallocAsync(&block, block_bytes, st);
+    int got = 0;
+    for (; !e && got < cnt; ++got)
+        e = cudaMallocAsync((void **)&rs[got]->result,
+                            sizeof(double) * result_doubles(rs[got]->in), st);
+    if (e) {                        // out of device memory now: retry later
+        for (int i = 0; i < got; ++i) {
+            cudaFreeAsync(rs[i]->result, st);
+            rs[i]->result = nullptr;
+        }
+        if (block) cudaFreeAsync(block, st);
+        cudaGetLastError();
+        return 0;
+    }
+    std::vector<const double *> d(cnt), z(cnt);
+    std::vector<double> alpha(cnt);
+    std::vector<double *> lam(cnt), V(cnt);
+    std::vector<const int *> cntp(cnt);
+    for (int i = 0; i < cnt; ++i) {
+        Req *r = rs[i];
+        const size_t n = (size_t)r->in.n;
+        r->lam = r->result;
+        r->V = r->in.want_vectors ? r->result + n : nullptr;
+        r->U = nullptr;
+        d[i] = r->in.d;
+        z[i] = r->in.z;
+        alpha[i] = r->in.alpha;
+        lam[i] = r->lam;
+        V[i] = r->V;
+    }
+    // (the run shares want_vectors, so a pass writes columns for all or none)
+    e = ae::launch_req_batch(cnt, ns.data(), d.data(), z.data(), alpha.data(), lam.data(),
+                             V.data(), block, ro, st, cntp.data());
+    for (int i = 0; i < cnt && !e; ++i)
+        e = cudaMemcpyAsync(rs[i]->cnt_host, cntp[i], sizeof(int) * ae::C_COUNT,
+                            cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaFreeAsync(block, st);
+    for (int i = 0; i < cnt && !e; ++i) e = cudaEventRecord(rs[i]->done, st);
+    const size_t share = block_bytes / cnt;
+    for (int i = cnt - 1; i >= 0; --i) queue.erase(queue.begin() + at[i]);
+    for (int i = 0; i < cnt; ++i) {
+        Req *r = rs[i];
+        if (e) {
+            r->state = AE_REQ_ERROR;
+            r->status = AE_ERR_CUDA;
+            continue;
+        }
+        r->slot = slot;
+        r->state = AE_REQ_RUNNING;
+        r->bytes = sizeof(double) * result_doubles(r->in) + share;
+        in_use += r->bytes;
+        r->charged = true;
+        inflight.push_back(r);
+        ++admitted;
+        ++merged;
+    }
+    if (e) {
+        worker_error = e;
+        return cnt;
+    }
+    slot_busy[slot] = cnt;          // freed as its requests retire
+    return cnt;
+}
 
 bool ae_server::admit_locked(Req *r) {
     int slot = -1;
@@ -152,7 +266,7 @@ bool ae_server::admit_locked(Req *r) {
 
 void ae_server::retire_locked(Req *r) {
     r->t_done = clk::now();
-    slot_busy[r->slot] = 0;
+    if (slot_busy[r->slot] > 0) --slot_busy[r->slot];
     const int *c = r->cnt_host;
     if (c[ae::C_FLAGS] & ae::CF_BAD) r->status = AE_ERR_INPUT;
     else if (c[ae::C_CAPPED]) r->status = AE_ERR_NOCONV;
@@ -182,8 +296,12 @@ void ae_server::loop() {
                 ++i;
             }
         }
-        // 2. admit in FIFO order
-        while (!queue.empty() && admit_locked(queue.front())) queue.pop_front();
+        // 2. admit in FIFO order (a run of small arrowheads at the head as one)
+        while (!queue.empty()) {
+            if (admit_merged_locked() > 0) continue;
+            if (!admit_locked(queue.front())) break;
+            queue.pop_front();
+        }
         if (inflight.empty() && queue.empty()) {
             cv.wait_for(lk, std::chrono::milliseconds(5));
         } else {
@@ -345,6 +463,7 @@ int ae_serve_stats(ae_server *s, ae_serve_stats_t *st) {
         st->eigenpairs_per_s = span > 0 ? s->eigenpairs / span : 0.0;
     }
     st->cuda_error = s->worker_error;
+    st->merged = s->merged;
     return AE_OK;
 }
 

@@ -322,16 +322,17 @@ template <class Team>
 __device__ __forceinline__ double secular_sum_stored(const double2 *buf, int m, const Team &T,
                                                      double x) {
     double acc0 = 0.0, acc1 = 0.0;
+    const double one = unit_reg();
     int j = T.rank;
     for (; j + Team::size < m; j += 2 * Team::size) {
         const double2 a = buf[j];
         const double2 b = buf[j + Team::size];
-        acc0 = fma(a.y, rcp(fma(-x, a.x, 1.0)), acc0);
-        acc1 = fma(b.y, rcp(fma(-x, b.x, 1.0)), acc1);
+        acc0 = fma(a.y, rcp_o(fma(-x, a.x, one), one), acc0);
+        acc1 = fma(b.y, rcp_o(fma(-x, b.x, one), one), acc1);
     }
     if (j < m) {
         const double2 a = buf[j];
-        acc0 = fma(a.y, rcp(fma(-x, a.x, 1.0)), acc0);
+        acc0 = fma(a.y, rcp_o(fma(-x, a.x, one), one), acc0);
     }
     return T.sum(acc0 + acc1);
 }
@@ -343,12 +344,13 @@ template <class Team>
 __device__ __forceinline__ double2 secular_sum_d_stored(const double2 *buf, int m,
                                                         const Team &T, double x) {
     double s0 = 0.0, s1 = 0.0, d0 = 0.0, d1 = 0.0;
+    const double one = unit_reg();
     int j = T.rank;
     for (; j + Team::size < m; j += 2 * Team::size) {
         const double2 a = buf[j];
         const double2 b = buf[j + Team::size];
-        const double ra = rcp(fma(-x, a.x, 1.0));
-        const double rb = rcp(fma(-x, b.x, 1.0));
+        const double ra = rcp_o(fma(-x, a.x, one), one);
+        const double rb = rcp_o(fma(-x, b.x, one), one);
         const double qa = a.y * ra, qb = b.y * rb;
         s0 += qa;
         s1 += qb;
@@ -357,7 +359,7 @@ __device__ __forceinline__ double2 secular_sum_d_stored(const double2 *buf, int 
     }
     if (j < m) {
         const double2 a = buf[j];
-        const double ra = rcp(fma(-x, a.x, 1.0));
+        const double ra = rcp_o(fma(-x, a.x, one), one);
         const double qa = a.y * ra;
         s0 += qa;
         d0 = fma(qa, a.x * ra, d0);
@@ -613,6 +615,7 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
                                         double wscale, double2 *buf = nullptr, int q = -1) {
     dd s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
     int c1 = 0, c2 = 0;
+    const double one = unit_reg();
     double pmax = -INFINITY, pmin = INFINITY, up = -INFINITY, lo = INFINITY, wsum = 0.0,
            usq = 0.0;
     auto term = [&](int j, double &dhi, double &uacc) -> dd {
@@ -621,13 +624,13 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
         if (DD) {
             del = R.shifted_dd(j, shift, skip);
             const dd z2 = R.z2_dd(j);
-            p = rcp(del.hi);
+            p = rcp_o(del.hi, one);
             q1 = z2.hi * p;
             const double res = fma(-q1, del.lo, fma(-q1, del.hi, z2.hi) + z2.lo);
             q2 = res * p;
         } else {
             del = dd{R.shifted(j, shift, skip), 0.0};
-            p = rcp(del.hi);
+            p = rcp_o(del.hi, one);
             q1 = R.z2(j) * p;
         }
         if (buf) buf[j] = make_double2(del.hi, q1);   // (delta_j, zeta_j^2 / delta_j)

@@ -115,3 +115,21 @@ def test_part_buffer_too_small_is_refused(ae):
     with pytest.raises(ae.AeError) as ei:
         ae.arrow_eig_part(t(d), t(z), a, 4, 4, cap=10)
     assert ei.value.status == -5
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 9])
+def test_more_parts_than_eigenpairs(ae, n):
+    # parts may be empty (nparts > m + 1); the non-empty ones still tile the output
+    d, z, a = W.uniform_arrow(n, seed=90 + n)
+    whole = ae.arrow_eig(t(d), t(z), a)
+    torch.cuda.synchronize()
+    nparts = n + 3
+    blocks = []
+    for p in range(nparts):
+        r = ae.arrow_eig_part(t(d), t(z), a, p, nparts)
+        torch.cuda.synchronize()
+        if r["count"]:
+            blocks.append((r["pos0"], r["lam"].cpu().numpy(), r["V"].cpu().numpy()))
+    lam, V = shard.merge_parts(n, blocks)
+    np.testing.assert_array_equal(lam, whole["lam"].cpu().numpy())
+    np.testing.assert_array_equal(V, whole["V"].cpu().numpy())
