@@ -584,6 +584,7 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
         }
         if (!col) return;
         // 1/(shifted difference of row r - mu); 0 for a zero spike
+        const double unit = unit_reg();
         auto recip = [&](int r) {
             if (spk[r] == 0.0) return 0.0;
             double del;
@@ -598,7 +599,7 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
             } else {
                 del = key[r] - sig;
             }
-            return rcp(del - mu);
+            return rcp_o(del - mu, unit);
         };
         // component of row r of x = [(D - lambda I)^{-1} spikes; -1]
         auto comp = [&](int r) { return spk[r] * recip(r); };
@@ -631,9 +632,8 @@ __device__ void vector_item(int n, int n1, const double *__restrict__ key,
                           !(S.cnt[C_FLAGS] & CF_UNSORTED);
         if (fast) {
             const double2 *P = reinterpret_cast<const double2 *>(stage);
-            const double one = unit_reg();
             auto one_d = [&](int r, double del, double &acc) {
-                const double t = rcp_o(del - mu, one);
+                const double t = rcp_o(del - mu, unit);
                 const double x = spk[r] * t;
                 keep[RS * r] = (CPLX || TWO) ? t : x;
                 acc = fma(x, x, acc);

@@ -293,24 +293,25 @@ template <class P, class Team>
 __device__ __forceinline__ double secular_sum(const P &R, const Team &T, double shift, int skip,
                                               double x) {
     double acc0 = 0.0, acc1 = 0.0;
+    const double one = unit_reg();
     int j = T.rank;
     for (; j + Team::size < R.m; j += 2 * Team::size) {
         if (j != skip) {
             const double dj = R.shifted(j, shift, skip);
-            const double t = fma(-x, dj, 1.0);
-            acc0 = fma(R.z2(j), rcp(dj * t), acc0);
+            const double t = fma(-x, dj, one);
+            acc0 = fma(R.z2(j), rcp_o(dj * t, one), acc0);
         }
         const int j2 = j + Team::size;
         if (j2 != skip) {
             const double dj = R.shifted(j2, shift, skip);
-            const double t = fma(-x, dj, 1.0);
-            acc1 = fma(R.z2(j2), rcp(dj * t), acc1);
+            const double t = fma(-x, dj, one);
+            acc1 = fma(R.z2(j2), rcp_o(dj * t, one), acc1);
         }
     }
     if (j < R.m && j != skip) {
         const double dj = R.shifted(j, shift, skip);
-        const double t = fma(-x, dj, 1.0);
-        acc0 = fma(R.z2(j), rcp(dj * t), acc0);
+        const double t = fma(-x, dj, one);
+        acc0 = fma(R.z2(j), rcp_o(dj * t, one), acc0);
     }
     return T.sum(acc0 + acc1);
 }
