@@ -1,5 +1,7 @@
-// ae_arrow.cu -- the eigen-solver pipeline on one stream, for the three
-// problem kinds that reduce to a real symmetric arrowhead:
+// ae_arrow.cu -- the eigen-solver pipeline on one stream, for the problem
+// kinds that reduce to a real symmetric arrowhead (the kernels after the
+// reduction are in ae_solve.cuh; this unit instantiates them for the
+// arrowhead, ae_solve_*.cu for the other kinds):
 //   ARROW  A = [diag(d) z; z^T alpha]                       (Sec. 1)
 //   DPR1   M = diag(d) + rho u u^T, via A = L^{-1} M L        (Sec. 6.3)
 //   SVD    B = [diag(d) z; 0 alpha], via A = B^T B            (Sec. 6.2)
@@ -25,6 +27,7 @@
 
 #include "ae_internal.h"
 #include "ae_pipeline.cuh"
+#include "ae_solve.cuh"
 
 namespace ae {
 
@@ -123,155 +126,6 @@ __global__ void __launch_bounds__(1024) k_post(int n1, const double *__restrict_
     post_block<K>(n1, d, z, zrow, alpha, rho_abs, S);
 }
 
-// ---------------------------------------------------------------------------
-// eigenpairs
-// ---------------------------------------------------------------------------
-// With va.fused, each warp writes eigenpair k's column right after solving it
-// (pass 1 staged in its stored-pair slice, which the solve no longer needs), at
-// the position k + #(deflated values >= lambda_k) that the placement gives.
-template <Kind K, Kind VK>
-__global__ void __launch_bounds__(256, 3) k_eig(Scratch S, SolveOpts o, VecArgs va) {
-    const int lane = threadIdx.x & 31;
-    const int m = S.cnt[C_M];
-    const auto R = PolesOf<K>::make(S, m);
-    const WarpTeam T{lane};
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    double2 *buf = S.wbuf ? S.wbuf + gw * S.wstride : nullptr;
-    // a part also solves the eigenpair on each side of its range (Algorithm
-    // 1's solve only, the same bits its owner computes): the remedy decision
-    // of Eq. (K0) needs both neighbours.  Its tickets start at its first such
-    // eigenpair (k_part sets the counter); the range is re-read per item
-    // rather than held in registers across the solve.
-    const int k_hi = S.cnt[C_PART] ? S.cnt[C_KHI] : m + 1;
-    for (;;) {
-        int k = 0;
-        if (lane == 0) k = atomicAdd(S.cnt + C_WORK, 1);
-        k = __shfl_sync(FULL, k, 0);
-        if (k >= k_hi) break;
-        eig_item<K>(R, T, S, k, o, buf);
-        if (va.fused && (!__ldcg(S.cnt + C_PART) ||
-                         (k >= __ldcg(S.cnt + C_K0) && k < __ldcg(S.cnt + C_K1)))) {
-            __syncwarp();
-            if (lane == 0) {
-                place_item(S, k);
-                S.pos0[k] = S.pos[k];
-            }
-            __syncwarp();
-            vector_item<VK>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn, S,
-                            va.out, k, T, (double *)buf, true, true);
-        }
-    }
-}
-
-// Remedy decisions: one thread per eigenpair (of the part).  The solves on a
-// DPR1 inverse (Remarks 1, 2(b)), which add a double-double pass, are listed
-// from the front of the n-entry list and the others from its back, so that
-// the remedy kernel deals the costlier ones out first, one per SM in turn.
-__global__ void k_fix_decide(Kind kind, Scratch S, double knu_max, int n) {
-    const PartRange P = part_range(S);
-    const int k = P.k0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P.k1) return;
-    const int r = fix_decide_item(kind, S, k, knu_max);
-    if (r == AE_FLAG_OTHERPOLE) S.fixlist[n - 1 - atomicAdd(S.cnt + C_NFIX2, 1)] = k;
-    else if (r) S.fixlist[atomicAdd(S.cnt + C_NFIX, 1)] = k;
-}
-
-// remedy w of the list k_fix_decide wrote (front part first, then the back)
-__device__ __forceinline__ int fix_at(const Scratch &S, long long w, int n) {
-    const int nf = S.cnt[C_NFIX];
-    return w < nf ? S.fixlist[w] : S.fixlist[n - 1 - (int)(w - nf)];
-}
-
-// Remedy solves by teams of NW warps (NW = 8, 4 or 2) that share their CTA:
-// team g of CTA b takes remedies w = g * grid + b, then w + teams, ... (so that
-// consecutive remedies land on different SMs), each on the stored-pair slice
-// of the team's first warp (the grid never exceeds k_eig's, so the slices
-// exist).  With va.fused the same team rewrites the remedied eigenpair's
-// column (its position recorded in pos0, as k_eig does).
-template <Kind K, Kind VK, int NW>
-__device__ __forceinline__ void fix_solve_teams(const Scratch &S, const SolveOpts &o,
-                                                const VecArgs &va, int nfix, double *red) {
-    constexpr int TPC = 8 / NW;                  // teams per CTA of 8 warps
-    const int m = S.cnt[C_M];
-    const auto R = PolesOf<K>::make(S, m);
-    const int g = (int)(threadIdx.x >> 5) / NW;
-    const CtaTeam<NW> T{(int)threadIdx.x - g * 32 * NW, red + 2 * NW * g, NW == 8 ? 0 : 1 + g};
-    const long long w0 = (long long)blockIdx.x * 8 + (long long)g * NW;
-    double2 *buf = S.wbuf ? S.wbuf + w0 * S.wstride : nullptr;
-    for (long long w = (long long)g * gridDim.x + blockIdx.x; w < nfix;
-         w += (long long)TPC * gridDim.x) {
-        const int k = fix_at(S, w, va.n);
-        const bool kept = fix_solve_item<K>(R, T, S, k, o, buf);
-        if (va.fused) {
-            T.sync();
-            if (T.rank == 0) {
-                place_item(S, k);
-                S.pos0[k] = S.pos[k];
-            }
-            T.sync();
-            vector_item<VK>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn, S,
-                            va.out, k, T, (double *)buf, true, kept);
-        }
-        T.sync();                                // before buf and red are reused
-    }
-}
-
-// Remedy solves.  The team size is the largest of 8, 4, 2 warps that still
-// gives every listed eigenpair a team of its own (one wave over the grid);
-// with more remedies than half the grid's warps, one warp each, remedy w on
-// warp w / CTAs of CTA w mod CTAs: spread over all SMs.
-template <Kind K, Kind VK>
-__global__ void __launch_bounds__(256) k_fix_solve(Scratch S, SolveOpts o, VecArgs va) {
-    __shared__ double red[16];
-    const int nfix = S.cnt[C_NFIX] + S.cnt[C_NFIX2];
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    if (nfix == 0) return;
-    if (nwarps / 8 >= nfix) {
-        fix_solve_teams<K, VK, 8>(S, o, va, nfix, red);
-    } else if (nwarps / 4 >= nfix) {
-        fix_solve_teams<K, VK, 4>(S, o, va, nfix, red);
-    } else if (nwarps / 2 >= nfix) {
-        fix_solve_teams<K, VK, 2>(S, o, va, nfix, red);
-    } else {
-        const int m = S.cnt[C_M];
-        const auto R = PolesOf<K>::make(S, m);
-        const int lane = threadIdx.x & 31;
-        const WarpTeam T{lane};
-        const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        double2 *buf = S.wbuf ? S.wbuf + gw * S.wstride : nullptr;
-        // (tickets would hand consecutive remedies to the warps of the first
-        // CTAs to arrive, on a few SMs)
-        const int wi = threadIdx.x >> 5;
-        for (long long w = (long long)wi * gridDim.x + blockIdx.x; w < nfix;
-             w += (long long)(blockDim.x >> 5) * gridDim.x) {
-            const int k = fix_at(S, w, va.n);
-            const bool kept = fix_solve_item<K>(R, T, S, k, o, buf);
-            if (va.fused) {
-                __syncwarp();
-                if (lane == 0) {
-                    place_item(S, k);
-                    S.pos0[k] = S.pos[k];
-                }
-                __syncwarp();
-                vector_item<VK>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn,
-                                S, va.out, k, T, (double *)buf, true, kept);
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// output placement and vectors
-// ---------------------------------------------------------------------------
-__global__ void k_place(Scratch S) {
-    const PartRange P = part_range(S);
-    const int ncomp = S.cnt[C_M] + 1;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nk = P.k1 - P.k0;
-    if (i < nk) place_item(S, P.k0 + i);
-    else if (i < nk + P.u1 - P.u0) place_item(S, ncomp + P.u0 + (i - nk));
-}
-
 // One part of a split solve: its eigenpair range (an even split of the m + 1
 // computed eigenpairs), its deflated rows and its first output position.
 __global__ void k_part(Scratch S, int part, int nparts) {
@@ -290,31 +144,6 @@ __global__ void k_part(Scratch S, int part, int nparts) {
     S.cnt[C_WORK] = k0 > 0 ? k0 - 1 : 0;             // k_eig's first ticket
     S.cnt[C_KHI] = k1 < ncomp ? k1 + 1 : ncomp;
     S.cnt[C_PART] = 1;
-}
-
-// All columns, or with va.fused (k_eig and k_fix_solve wrote the computed
-// ones) only those whose final position differs from the one used then, and
-// the deflated ones; the scalar outputs of every item (K_nu and the remedy
-// flags are known only now).  Staged in the warps' stored-pair slices when
-// there are enough of them.
-template <Kind K>
-__global__ void __launch_bounds__(256) k_vectors(VecArgs va, Scratch S) {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int ncomp = S.cnt[C_M] + 1;
-    const PartRange P = part_range(S);
-    const int nk = P.k1 - P.k0;
-    const int nitems = nk + P.u1 - P.u0;
-    const WarpTeam T{lane};
-    double *stage = (S.wbuf && va.fused) ? (double *)(S.wbuf + (long long)warp * S.wstride)
-                                         : nullptr;
-    for (int i = warp; i < nitems; i += nwarps) {
-        const int item = i < nk ? P.k0 + i : ncomp + P.u0 + (i - nk);
-        const bool cols = !(va.fused && item < ncomp) || S.pos[item] != S.pos0[item];
-        vector_item<K>(va.n, va.n1, va.key, va.spk, va.z, va.zrow, va.alpha, va.sgn, S, va.out,
-                       item, T, stage, cols);
-    }
 }
 
 __global__ void k_debug_rcp(int n, const double *x, double *y) {
@@ -391,18 +220,9 @@ Scratch carve_scratch(void *base, int n) {
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
-static int sm_count() {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-        if (cached <= 0) cached = 1;
-    }
-    return cached;
-}
-
 // CTAs of k_eig: enough for every eigenpair, at most what stays resident
+// (every kind's k_eig has the same launch bounds, so the arrowhead's
+// occupancy holds for all; the stored-pair slices are allocated for this grid)
 static int eig_grid(int n) {
     static int per_sm = 0;
     if (!per_sm) {
@@ -416,38 +236,6 @@ static int eig_grid(int n) {
 }
 
 int eig_grid_warps(int n) { return eig_grid(n) * 8; }
-
-// K: the arrowhead the kernels solve; VK: the kind of the vector epilogue
-// (Hermitian and non-symmetric inputs solve the real arrowhead of their moduli)
-template <Kind K, Kind VK>
-static void launch_pipeline(int n, Scratch S, const SolveOpts &so, const RunOpts &ro,
-                            const VecArgs &va, cudaStream_t st) {
-    const int sms = sm_count();
-    const int grid = eig_grid(n);
-    if (ro.ev[1]) cudaEventRecord(ro.ev[1], st);
-    k_eig<K, VK><<<grid, 256, 0, st>>>(S, so, va);
-    if (ro.ev[2]) cudaEventRecord(ro.ev[2], st);
-    if (ro.fixup) {
-        k_fix_decide<<<(n + 255) / 256, 256, 0, st>>>(K, S, ro.knu_max, n);
-        // every CTA resident at once (the remedies are assigned statically)
-        static int fix_per_sm = 0;
-        if (!fix_per_sm) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fix_per_sm, k_fix_solve<K, VK>, 256, 0);
-            if (fix_per_sm <= 0) fix_per_sm = 1;
-        }
-        int fgrid = sms * fix_per_sm;
-        fgrid = fgrid < grid ? fgrid : grid;
-        fgrid = n < fgrid ? n : fgrid;
-        k_fix_solve<K, VK><<<fgrid, 256, 0, st>>>(S, so, va);
-    }
-    if (ro.ev[3]) cudaEventRecord(ro.ev[3], st);
-    k_place<<<(n + 255) / 256, 256, 0, st>>>(S);
-    // fused: one warp per stored-pair slice, so every warp can stage
-    int vgrid = (n + 7) / 8;
-    const int vcap = va.fused ? grid : sms * 16;
-    vgrid = vgrid < vcap ? vgrid : vcap;
-    k_vectors<VK><<<vgrid, 256, 0, st>>>(va, S);
-}
 
 cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, double alpha,
                          double rho, const Outputs &out, const RunOpts &ro, Scratch S,
@@ -476,26 +264,27 @@ cudaError_t launch_solve(Kind kind, int n, const double *d, const double *z, dou
     k_reduce<<<1, 1024, 0, st>>>(n1, key, spk, S.perm, S);
     SolveOpts so{ro.max_iter, ro.precision, ro.finish, ro.bgate, ro.kb_max};
     VecArgs va{n, n1, key, spk, z, zrow, alpha, sgn, out, (S.wbuf && out.V) ? 1 : 0};
+    const int grid = eig_grid(n);
     switch (kind) {
         case KIND_ARROW:
             k_post<KIND_ARROW><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
-            launch_pipeline<KIND_ARROW, KIND_ARROW>(n, S, so, ro, va, st);
+            launch_pipeline<KIND_ARROW, KIND_ARROW>(n, grid, S, so, ro, va, st);
             break;
         case KIND_DPR1:
             k_post<KIND_DPR1><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, fabs(rho), S);
-            launch_pipeline<KIND_DPR1, KIND_DPR1>(n, S, so, ro, va, st);
+            launch_pipeline_dpr1(n, grid, S, so, ro, va, st);
             break;
         case KIND_TSVD:
             k_post<KIND_TSVD><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
-            launch_pipeline<KIND_TSVD, KIND_TSVD>(n, S, so, ro, va, st);
+            launch_pipeline_tsvd(n, grid, S, so, ro, va, st);
             break;
         case KIND_HERM:
             k_post<KIND_HERM><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
-            launch_pipeline<KIND_ARROW, KIND_HERM>(n, S, so, ro, va, st);
+            launch_pipeline_herm(n, grid, S, so, ro, va, st);
             break;
         case KIND_NSYM:
             k_post<KIND_NSYM><<<1, 1024, 0, st>>>(n1, d, z, zrow, alpha, 0.0, S);
-            launch_pipeline<KIND_ARROW, KIND_NSYM>(n, S, so, ro, va, st);
+            launch_pipeline_nsym(n, grid, S, so, ro, va, st);
             break;
     }
     if (ro.ev[4]) cudaEventRecord(ro.ev[4], st);
@@ -527,7 +316,7 @@ cudaError_t launch_arrow_part(int n, const double *d, const double *z, double al
     if (!out.lambda || *count > cap) return cudaSuccess;   // size query, or no room
     const SolveOpts so{ro.max_iter, ro.precision, ro.finish, ro.bgate, ro.kb_max};
     const VecArgs va{n, n1, d, z, z, nullptr, alpha, 1.0, out, (S.wbuf && out.V) ? 1 : 0};
-    launch_pipeline<KIND_ARROW, KIND_ARROW>(n, S, so, ro, va, st);
+    launch_pipeline<KIND_ARROW, KIND_ARROW>(n, eig_grid(n), S, so, ro, va, st);
     if (ro.ev[4]) cudaEventRecord(ro.ev[4], st);
     return cudaGetLastError();
 }
