@@ -527,6 +527,29 @@ int ae_fma_peaks(double *fp64_tflops, double *fp32_tflops, void *stream);
  */
 int ae_debug_rcp(int n, const double *x, double *y, void *stream);
 
+/*
+ * ae_debug_newton -- the solver's bracketed FP64 finish (the Newton
+ * alternative to Algorithm 3's bisection) on one shifted inverse's Pick
+ * function F(x) = (b - x) - c (sum_j cj[j] / (1 - x delta[j]) - 1/x), for
+ * testing its termination and result from a given start.
+ *   m, delta, cj  the m shifted differences delta_j = d_j - sigma (j != i) and
+ *                 cj_j = zeta_j^2 / delta_j (device arrays)
+ *   b, c          the inverse's element b and c = 1 / zeta_i^2 (> 0)
+ *   side          +1: the zero lies right of all poles, -1: left (-6 else)
+ *   pole          F's pole nearest that side (1/delta_{i-+1}, or 0)
+ *   left < right  a bracket of the zero (-8 else)
+ *   x0            first trial point (NaN: the bracket's middle)
+ *   dF0, xdF0, rel0  an F' estimate (NaN: none), the point it was taken at
+ *                 (NaN: unknown) and its relative error bound (INFINITY: none)
+ *   max_iter      cap on FP64 evaluations (>= 1)
+ *   out           device double[3]: nu (the final bracket's right end), the
+ *                 FP64 evaluations, those that also formed F'
+ * Runs on one thread; returns AE_OK, -k for argument k, or AE_ERR_CUDA.
+ */
+int ae_debug_newton(int m, const double *delta, const double *cj, double b, double c, int side,
+                    double pole, double left, double right, double x0, double dF0, double xdF0,
+                    double rel0, int max_iter, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

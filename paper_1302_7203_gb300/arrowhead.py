@@ -38,7 +38,7 @@ EXPORTED = ["ae_default_opts", "ae_status_string", "ae_last_cuda_error", "arrow_
             "ae_team_width", "ae_serve_create", "ae_serve_submit", "ae_serve_poll",
             "ae_serve_result", "ae_serve_release", "ae_serve_stats", "ae_serve_destroy",
             "arrow_eig_host", "arrow_eig_noalloc", "arrow_eig_part", "arrow_eig_part_size",
-            "ae_fma_peaks", "ae_debug_rcp"]
+            "ae_fma_peaks", "ae_debug_rcp", "ae_debug_newton"]
 AE_EAGAIN = 1005
 KIND_ARROW, KIND_DPR1, KIND_SVD = 0, 1, 2
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
@@ -179,6 +179,8 @@ def lib():
         L.ae_fma_peaks.restype = I
         L.ae_debug_rcp.argtypes = [I, P, P, P]
         L.ae_debug_rcp.restype = I
+        L.ae_debug_newton.argtypes = [I, P, P, D, D, I, D, D, D, D, D, D, D, I, P, P]
+        L.ae_debug_newton.restype = I
         _lib = L
         return L
 
@@ -725,6 +727,22 @@ def debug_rcp(x, stream=None):
     _check("ae_debug_rcp", lib().ae_debug_rcp(int(x.numel()), _ptr(x), _ptr(y),
                                               _stream_handle(stream)))
     return y
+
+
+def debug_newton(delta, cj, b, c, side, pole, left, right, x0=float("nan"),
+                 dF0=float("nan"), xdF0=float("nan"), rel0=float("inf"), max_iter=300,
+                 stream=None):
+    """The solver's FP64 finish on one shifted inverse's Pick function
+    (include/arrowhead.h, ae_debug_newton).  delta, cj: float64 CUDA tensors.
+    Returns (nu, FP64 evaluations, evaluations with F')."""
+    import torch
+    out = torch.empty(3, dtype=torch.float64, device=delta.device)
+    _check("ae_debug_newton", lib().ae_debug_newton(
+        int(delta.numel()), _ptr(delta), _ptr(cj), float(b), float(c), int(side), float(pole),
+        float(left), float(right), float(x0), float(dF0), float(xdF0), float(rel0),
+        int(max_iter), _ptr(out), _stream_handle(stream)))
+    nu, it, itd = out.cpu().tolist()
+    return nu, int(it), int(itd)
 
 
 def exported_symbols(path=LIB_PATH):

@@ -412,4 +412,20 @@ int ae_debug_rcp(int n, const double *x, double *y, void *stream) {
     return e == cudaSuccess ? AE_OK : cuda_fail(e);
 }
 
+int ae_debug_newton(int m, const double *delta, const double *cj, double b, double c, int side,
+                    double pole, double left, double right, double x0, double dF0, double xdF0,
+                    double rel0, int max_iter, double *out, void *stream) {
+    if (m < 0) return -1;
+    if (m > 0 && !delta) return -2;
+    if (m > 0 && !cj) return -3;
+    if (!(c > 0.0) || !isfinite(b)) return -4;
+    if (side != 1 && side != -1) return -6;
+    if (!(left < right)) return -8;
+    if (max_iter < 1) return -14;
+    if (!out) return -15;
+    const ae::DebugNewton a{b, c, pole, left, right, x0, dF0, xdF0, rel0, side, max_iter};
+    cudaError_t e = ae::launch_debug_newton(m, delta, cj, a, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? AE_OK : cuda_fail(e);
+}
+
 }  // extern "C"

@@ -151,6 +151,36 @@ __global__ void k_debug_rcp(int n, const double *x, double *y) {
     if (i < n) y[i] = rcp(x[i]);
 }
 
+// The FP64 finish (newton_finish) on the shifted inverse's Pick function
+// F(x) = (b - x) - c (sum_j cj_j / (1 - x delta_j) - 1/x), kappa = -1, from a
+// caller's bracket, start and F' estimate; one thread.  out: nu (the right end
+// of the final bracket), the FP64 evaluations, those with F'.
+__global__ void k_debug_newton(int m, const double *__restrict__ delta,
+                               const double *__restrict__ cj, DebugNewton a, double *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    auto FD = [&](double x, bool need_d, double &dF, double &err) {
+        double S = 0.0, Sd = 0.0;
+        for (int j = 0; j < m; ++j) {
+            const double t = rcp(fma(-x, delta[j], 1.0));
+            const double q = cj[j] * t;
+            S += q;
+            if (need_d) Sd = fma(q * delta[j], t, Sd);
+        }
+        const double rx = rcp(x);
+        if (need_d) dF = -1.0 - a.c * fma(rx, rx, Sd);
+        err = 0x1p-52 * (fabs(a.b) + fabs(x) + a.c * (fabs(S) + fabs(rx)));
+        return (a.b - x) - a.c * (S - rx);
+    };
+    double left = a.left, right = a.right;
+    bool fb;
+    int itd = 0;
+    const int it = newton_finish(FD, a.side, a.pole, -1.0, left, right, true, true, a.max_iter,
+                                 left, right, fb, a.dF0, &itd, a.x0, a.c, a.xdF0, a.rel0);
+    out[0] = right;
+    out[1] = (double)it;
+    out[2] = (double)itd;
+}
+
 // ---------------------------------------------------------------------------
 // scratch layout
 // ---------------------------------------------------------------------------
@@ -323,6 +353,12 @@ cudaError_t launch_arrow_part(int n, const double *d, const double *z, double al
 
 cudaError_t launch_debug_rcp(int n, const double *x, double *y, cudaStream_t st) {
     if (n > 0) k_debug_rcp<<<(n + 255) / 256, 256, 0, st>>>(n, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_newton(int m, const double *delta, const double *cj,
+                                const DebugNewton &a, double *out, cudaStream_t st) {
+    k_debug_newton<<<1, 32, 0, st>>>(m, delta, cj, a, out);
     return cudaGetLastError();
 }
 

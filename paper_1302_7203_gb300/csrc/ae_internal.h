@@ -148,6 +148,13 @@ cudaError_t launch_arrow_part(int n, const double *d, const double *z, double al
                               int nparts, int cap, const Outputs &out, const RunOpts &ro,
                               Scratch S, cudaStream_t st, int *pos0, int *count);
 cudaError_t launch_debug_rcp(int n, const double *x, double *y, cudaStream_t st);
+// arguments of the FP64-finish test hook (ae_debug_newton)
+struct DebugNewton {
+    double b, c, pole, left, right, x0, dF0, xdF0, rel0;
+    int side, max_iter;
+};
+cudaError_t launch_debug_newton(int m, const double *delta, const double *cj,
+                                const DebugNewton &a, double *out, cudaStream_t st);
 // Requests of the serving loop solved together by the batched stages (see
 // ae_batch.cu): the device block they need, and the launch.
 size_t req_batch_bytes(int count, const int *ns);

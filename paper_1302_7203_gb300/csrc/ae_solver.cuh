@@ -846,11 +846,15 @@ __device__ bool fp32_verify(int dir, F64 f64, double l, double r, double &left, 
 // evaluations; `fell_back` reports a failed check.
 // ---------------------------------------------------------------------------
 // F' is evaluated (3 more FP64 instructions a term) only when the last step
-// was longer than 2^-26 |x|: after a shorter one the previous F' is within
-// that relative distance of the current one, enough for a step whose own
-// length is below 2^-26 |x|.  dF0 (finite): an estimate of F' at the start that
-// is that good already (the caller's bracket is that tight), so the first
-// evaluation skips F' too.
+// was longer than 2^-26 rho, rho = |x - pole| the distance to F's nearest
+// pole (F' = kappa - sum_k W_k / (x - p_k)^2 changes by a factor within
+// 1 +- 2 |h| / rho over a step h): after a shorter one the previous F' is
+// within 2^-25 relative of the current one, enough for a step whose own
+// length is below 2^-26 rho.  (A bound relative to |x| instead lets a stale F'
+// from nearer the pole, where |F'| is larger, shorten every step below the
+// bound, so that F' is never re-evaluated and the bracket creeps.)  dF0
+// (finite): an estimate of F' at the start that is that good already (the
+// caller's bracket is that tight), so the first evaluation skips F' too.
 //
 // Local expansion (ca finite).  Both functions searched here have the form
 // F(x) = kappa x + const + K (S(x) - 1/x) with the terms q_j = c_j / (1 - x delta_j)
@@ -974,7 +978,7 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
             }
             nudged = nudge;
             pside = pos;
-            need_d = !(fabs(xn - x) < 0x1p-26 * fabs(x));
+            need_d = !(fabs(xn - x) < 0x1p-26 * fabs(x - pole));
             x = xn;
         }
         need_d = true;
@@ -1143,9 +1147,10 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                     x = xn;
                 }
                 x0 = x;
-                // an FP32 step that short leaves F' known to FP32 accuracy, which
-                // serves as the first FP64 evaluation's F'
-                if (step < 0x1p-20 * fabs(x0)) dF0 = dF32;
+                // an FP32 step that short (against the distance to the nearest
+                // pole) leaves F' known to FP32 accuracy, which serves as the
+                // first FP64 evaluation's F'
+                if (step < 0x1p-20 * fabs(x0 - pole)) dF0 = dF32;
             } else {
                 res.flags |= 64;
             }

@@ -214,3 +214,57 @@ def test_extreme_power_of_two_scaling(ae, e, form):
         tol = 10 * len(d) * 2.0 ** -53
         assert np.all(np.abs(g1["lam"] - g0["lam"] * s) <= tol * np.abs(g0["lam"] * s))
         assert np.all(np.abs(g1["V"] - g0["V"]) <= tol * np.abs(g0["V"]) + 1e-300)
+
+
+def _pick_function(k):
+    # the shifted inverse of the n = 16384 graded matrix at eigenvalue k's pole
+    # sigma (the oracle's shift), as the finish sees it: differences, c_j, b, c
+    import math
+    n = 16384
+    d, z, a = W.graded_arrow(n, seed=1)
+    order = np.argsort(-d)
+    ds, zs = d[order], np.abs(z[order])
+    ref = oracle.arrow_eig(d, z, a, ks=[k], vectors=False)
+    sigma = ref["sigma"][0]
+    i = int(np.flatnonzero(ds == sigma)[0])
+    nu = 1.0 / (ref["mu_hi"][0] + ref["mu_lo"][0])
+    keep = np.arange(n - 1) != i
+    delta = ds[keep] - sigma
+    cj = zs[keep] ** 2 / delta
+    c = 1.0 / zs[i] ** 2
+    b = math.fsum(list(cj) + [-(a - sigma)]) * c
+    side = 1 if nu > 0 else -1
+    jn = i - 1 if side > 0 else i + 1
+    pole = 1.0 / (ds[jn] - sigma)
+    return delta, cj, b, c, side, pole, nu
+
+
+def _dF(delta, cj, c, x):
+    t = 1.0 / (1.0 - x * delta)
+    return -1.0 - c * (1.0 / x ** 2 + np.sum(cj * delta * t * t))
+
+
+@pytest.mark.parametrize("k", [6340, 9953])
+def test_stale_derivative_near_a_pole_does_not_stall(ae, k):
+    # two eigenvalues within 1e-11 of zero whose shifted inverse has its zero
+    # 5x (k = 6340) and 3x (k = 9953) farther out than its nearest pole.  A
+    # start 1e-7 (relative) beyond that pole, with F' taken 1e-9 beyond it (as
+    # a short FP32 opening step can hand over, |F'| there 10^4 too large):
+    # the finish must evaluate F' again once its steps stay short against the
+    # pole's distance, and close on the zero the oracle gives.  Reusing F'
+    # while steps were short against |x| kept every step short: 300 FP64
+    # evaluations ended next to the pole.
+    delta, cj, b, c, side, pole, nu = _pick_function(k)
+    far = nu * 8.0 if side < 0 else nu * 8.0
+    left, right = (far, pole) if side < 0 else (pole, far)
+    x0 = pole * (1.0 + 1e-7)
+    xs = pole * (1.0 + 1e-9)
+    dF0 = _dF(delta, cj, c, xs)
+    got, it, itd = ae.debug_newton(t(delta), t(cj), b, c, side, pole, left, right, x0=x0,
+                                   dF0=dF0, max_iter=300)
+    assert it < 40, (it, itd)
+    assert itd >= 1
+    assert abs(got - nu) <= 1e-12 * abs(nu), (got, nu)
+    # the same from the bracket's middle with no estimate
+    got2, it2, _ = ae.debug_newton(t(delta), t(cj), b, c, side, pole, left, right, max_iter=300)
+    assert it2 < 40 and abs(got2 - nu) <= 1e-12 * abs(nu)
