@@ -694,10 +694,18 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
             else add(s2, c2, t);
         }
     }
-    s1 = fast_two_sum(s1.hi, s1.lo);
-    s2 = fast_two_sum(s2.hi, s2.lo);
-    s1 = T.sum(s1);
-    s2 = T.sum(s2);
+    if (DD) {
+        s1 = fast_two_sum(s1.hi, s1.lo);
+        s2 = fast_two_sum(s2.hi, s2.lo);
+        s1 = T.sum(s1);
+        s2 = T.sum(s2);
+    } else {
+        // standard precision: every thread's partial is one double (lo = 0), so
+        // the team adds doubles too -- five more roundings on top of the L per
+        // thread, where a double-double reduction costs ~100 FP64 instructions
+        s1 = dd{T.sum(s1.hi), 0.0};
+        s2 = dd{T.sum(s2.hi), 0.0};
+    }
     PassA A;
     if (GERSH) {
         A.pmax = T.max(pmax);
@@ -726,7 +734,12 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
 // formula, the other from the product of the roots, B P - Wq.
 __device__ __forceinline__ void quad_roots(double B, double P, double Wq, double &xs,
                                            double &xb) {
-    const double sq = hypot(B - P, 2.0 * sqrt(Wq));
+    // sqrt((B - P)^2 + 4 Wq): one fused square root where neither square can
+    // overflow or lose its significance, else the scaled hypot
+    const double u = B - P;
+    const double sq = (fabs(u) < 0x1p500 && Wq < 0x1p996 && (fabs(u) > 0x1p-480 || Wq > 0x1p-960))
+                          ? sqrt(fma(u, u, 4.0 * Wq))
+                          : hypot(u, 2.0 * sqrt(Wq));
     const double s = B + P;
     if (s >= 0.0) {
         xb = 0.5 * (s + sq);
@@ -1125,16 +1138,17 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
             if (big > 0.0 && isfinite(big) && scd > 0x1p-120 && scd < 0x1p120 && isfinite(sh)) {
                 const float sc = (float)scd;
                 const double K = c * s / R.zs;
+                const double sinv = ldexp(1.0, -ilogb(big));   // 1/s, exact
                 double x = 0.5 * (left + right);
                 double dF32 = NAN, step = INFINITY;
                 for (int t = 0; t < 2; ++t) {
-                    const float y = (float)(x / s);
+                    const float y = (float)(x * sinv);
                     const double xe = s * (double)y;
                     const float2 Tf = secular_sum_f32_d(R, T, sh, sl, sc, i, y);
                     ++res.f32p;
                     const double rx = rcp(xe);
                     const double F = (b - xe) + c * rx - K * (double)Tf.x;
-                    const double dF = -1.0 - c * rx * rx - K * (double)Tf.y / s;
+                    const double dF = -1.0 - c * rx * rx - K * (double)Tf.y * sinv;
                     const double d0 = fabs(xe - pole);
                     const double beta = (-1.0 - dF) * d0 * d0;
                     const double a = F + xe + (side > 0 ? -beta : beta) / d0;
