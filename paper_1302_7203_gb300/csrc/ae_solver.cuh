@@ -734,12 +734,24 @@ __device__ __forceinline__ PassA pass_a(const P &R, const Team &T, double shift,
 // formula, the other from the product of the roots, B P - Wq.
 __device__ __forceinline__ void quad_roots(double B, double P, double Wq, double &xs,
                                            double &xb) {
-    // sqrt((B - P)^2 + 4 Wq): one fused square root where neither square can
-    // overflow or lose its significance, else the scaled hypot
-    const double u = B - P;
-    const double sq = (fabs(u) < 0x1p500 && Wq < 0x1p996 && (fabs(u) > 0x1p-480 || Wq > 0x1p-960))
-                          ? sqrt(fma(u, u, 4.0 * Wq))
-                          : hypot(u, 2.0 * sqrt(Wq));
+    // sqrt((B - P)^2 + 4 Wq) with one square root: both terms scaled by 2^-k,
+    // k from the larger one's exponent, so that nothing overflows and the
+    // result scales exactly with the problem (a power-of-two scaling of A
+    // moves k and nothing else)
+    const double u = B - P, w = 4.0 * Wq;
+    const int eu = (int)((__double_as_longlong(u) >> 52) & 0x7ff);   // biased exponents
+    const int ew = (int)((__double_as_longlong(w) >> 52) & 0x7ff);
+    const int k = max(eu, 1023 + ((ew - 1023) >> 1)) - 1023;
+    double sq;
+    if (eu > 0 && eu < 2047 && ew > 0 && ew < 2047 && k < 1023) {     // normal, finite
+        // 2^-k and 2^k from their bits (-1022 <= -k, k <= 1022): exact scalings
+        const double si = __longlong_as_double((long long)(1023 - k) << 52);
+        const double so = __longlong_as_double((long long)(1023 + k) << 52);
+        const double us = u * si, ws = (w * si) * si;
+        sq = sqrt(fma(us, us, ws)) * so;
+    } else {
+        sq = hypot(u, 2.0 * sqrt(Wq));
+    }
     const double s = B + P;
     if (s >= 0.0) {
         xb = 0.5 * (s + sq);
@@ -915,29 +927,34 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
             double F;
             if (fabs(x - xa) <= Ha && itl < 64) {
                 const double h = x - xa;
-                F = Fa + h * (dFa + (ca / xa) * (h / xa) / x);   // (no overflow)
+                const double ixa = rcp(xa);
+                F = Fa + h * (dFa + (ca * ixa) * (h * ixa) * rcp(x));   // (no overflow)
                 dF = dFa;
                 ++itl;
             } else {
                 F = fd(x, need_d, dF, err);
                 ++it;
                 itd += need_d ? 1 : 0;
+                // (reciprocals, not divisions, in this scalar bookkeeping: a
+                // few ulps here move no bound by more than its slack)
+                const double ix = rcp(x);
+                const double cxx = (ca * ix) * ix;              // ca / x^2
                 if (need_d) {
                     xsrc = x;
                     rsrc = 0x1p-40;
-                    KSs = dF - kappa + ca / x / x;
+                    KSs = dF - kappa + cxx;
                 }
                 Ha = -1.0;
                 if (isfinite(ca) && isfinite(rsrc)) {
                     const double rho = fabs(x - pole);
                     const double dist = fabs(x - xsrc);
-                    const double drel = rsrc + 4.0 * dist / rho;
+                    const double drel = rsrc + 4.0 * dist * rcp(rho);
                     double H = 0x1p-27 * rho;
-                    if (fabs(KSs) > 0.0) H = fmin(H, 0.25 * err / (drel * fabs(KSs)));
+                    if (fabs(KSs) > 0.0) H = fmin(H, 0.25 * err * rcp(drel * fabs(KSs)));
                     if (dist <= 0.125 * rho && H > 0.0) {
                         xa = x;
                         Fa = F;
-                        dFa = kappa + KSs - ca / x / x;
+                        dFa = kappa + KSs - cxx;
                         dF = dFa;
                         Ha = H;
                     }
@@ -969,7 +986,7 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
                 // beta = (kappa - F') (x - pole)^2 >= 0
                 const double d0 = fabs(x - pole);
                 const double beta = (kappa - dF) * d0 * d0;
-                const double a = F - kappa * x + (side > 0 ? -beta : beta) / d0;
+                const double a = F - kappa * x + (side > 0 ? -beta : beta) * rcp(d0);
                 if (kappa == 0.0) {
                     xn = pole - beta / a;
                 } else {                                 // kappa = -1
@@ -1151,7 +1168,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                     const double dF = -1.0 - c * rx * rx - K * (double)Tf.y * sinv;
                     const double d0 = fabs(xe - pole);
                     const double beta = (-1.0 - dF) * d0 * d0;
-                    const double a = F + xe + (side > 0 ? -beta : beta) / d0;
+                    const double a = F + xe + (side > 0 ? -beta : beta) * rcp(d0);
                     double xs, xb;
                     quad_roots(a, pole, beta, xs, xb);
                     const double xn = side > 0 ? xb : xs;
@@ -1194,7 +1211,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                 const double dF = -1.0 - c * fma(rx, rx, Sd.y);
                 const double d0 = fabs(x0 - pole);
                 const double beta = (-1.0 - dF) * d0 * d0;
-                const double a = F + x0 + (side > 0 ? -beta : beta) / d0;
+                const double a = F + x0 + (side > 0 ? -beta : beta) * rcp(d0);
                 double xs, xb;
                 quad_roots(a, pole, beta, xs, xb);
                 const double xn = side > 0 ? xb : xs;
@@ -1355,7 +1372,7 @@ __device__ EigResult solve_dpr1_shift(const P &R, const Team &T, double shift,
                 const double dF = sg * rho * fma(rx, rx, Sd.y);
                 const double d0 = fabs(x - pole);
                 const double beta = -dF * d0 * d0;
-                const double a = F + (side > 0 ? -beta : beta) / d0;
+                const double a = F + (side > 0 ? -beta : beta) * rcp(d0);
                 const double xn = pole - beta / a;
                 if (!(xn > left && xn < right)) break;
                 xdF0 = x;
