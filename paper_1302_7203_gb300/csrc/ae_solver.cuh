@@ -1051,9 +1051,10 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
         // then P and Q again in double-double (Theorem 6)
         A = newton ? pass_a<false, false>(R, T, sigma, i, wz, buf)
                    : pass_a<true, false>(R, T, sigma, i, wz, buf);
-        const double ratio = (R.zsum - zi) / zi;
-        const double Kb0 = (A.P.hi + A.Q.hi) / fabs(A.P.hi - A.Q.hi);
-        if (ratio > (double)(R.m + 1) && !(Kb0 <= o.kb_max)) {
+        // (both tests multiplied out: ratio = (zsum - zeta_i) / zeta_i > m + 1
+        // and K_b0 = (P + Q) / |P - Q| > kb_max, NaN or a zero P - Q included)
+        if (R.zsum - zi > (double)(R.m + 1) * zi &&
+            !(A.P.hi + A.Q.hi <= o.kb_max * fabs(A.P.hi - A.Q.hi))) {
             const PassA D = pass_a<false, true>(R, T, sigma, i, wz);
             A.P = D.P;
             A.Q = D.Q;
