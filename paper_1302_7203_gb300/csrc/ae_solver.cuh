@@ -860,11 +860,16 @@ __device__ bool fp32_verify(int dir, F64 f64, double l, double r, double &left, 
 //  * the zero of the one-pole model  a + kappa x + beta / (x - pole)  that
 //    matches F and F' at x (kappa = -1 for the shifted inverse's Pick
 //    function, 0 for the DPR1 secular function): the Newton step of a function
-//    dominated by its nearest pole, exact for a 2 x 2 arrowhead;
-//    lengthened to tol = 2^-52 |x| when shorter (which closes the bracket from
-//    the other side once the zero is that near);
+//    dominated by its nearest pole, exact for a 2 x 2 arrowhead; when the
+//    Newton step -F/F' is shorter than 2^-30 |x - pole|, that step instead
+//    (the two agree to that order, and the model's formula loses so short a
+//    step in rounding); either lengthened to tol = 2^-52 |x| when shorter
+//    (which closes the bracket from the other side once the zero is that near);
 //  * when that leaves the bracket, the last such point taken from the side
-//    whose steps do not overshoot (F > 0 for side > 0), else the midpoint.
+//    whose steps do not overshoot, else the midpoint.  The model puts all of
+//    F' beyond kappa on the nearest pole, so near x it is more convex than F:
+//    from the side of the zero away from that pole (F > 0 for side > 0) its
+//    zero lies past F's, from the pole's side (F < 0 for side > 0) short of it.
 // Ends lv / rv not yet evaluated in FP64 (from the FP32 phase) are checked
 // after the loop; a failed check is itself a good end on the other side, and
 // the search resumes from the known-good end.  Returns the number of FP64
@@ -982,22 +987,31 @@ __device__ __forceinline__ int newton_finish(FD fd, int side, double pole, doubl
                 jump = fmax(2.0 * err / fabs(dF), 2.0 * tol);
                 xn = x + towards * jump;
             } else {
-                // one-pole model a + kappa x + beta / (x - pole) through (x, F, F'):
-                // beta = (kappa - F') (x - pole)^2 >= 0
                 const double d0 = fabs(x - pole);
-                const double beta = (kappa - dF) * d0 * d0;
-                const double a = F - kappa * x + (side > 0 ? -beta : beta) * rcp(d0);
-                if (kappa == 0.0) {
-                    xn = pole - beta / a;
-                } else {                                 // kappa = -1
-                    double xs, xb;
-                    quad_roots(a, pole, beta, xs, xb);
-                    xn = side > 0 ? xb : xs;
+                const double hN = -F * rcp(dF);          // the Newton step (F' < 0)
+                if (fabs(hN) < 0x1p-30 * d0) {
+                    // a step this short agrees with the model's to 2^-30 of its
+                    // length, and the model's formula (differences of terms as
+                    // large as |x| and beta / d0) would lose it in rounding and
+                    // could point the wrong way
+                    xn = x + hN;
+                } else {
+                    // one-pole model a + kappa x + beta / (x - pole) through
+                    // (x, F, F'): beta = (kappa - F') (x - pole)^2 >= 0
+                    const double beta = (kappa - dF) * d0 * d0;
+                    const double a = F - kappa * x + (side > 0 ? -beta : beta) * rcp(d0);
+                    if (kappa == 0.0) {
+                        xn = pole - beta / a;
+                    } else {                             // kappa = -1
+                        double xs, xb;
+                        quad_roots(a, pole, beta, xs, xb);
+                        xn = side > 0 ? xb : xs;
+                    }
                 }
                 if (fabs(xn - x) < tol) {
                     xn = x + towards * tol;
                     nudge = true;
-                } else if (pos == (side > 0)) {
+                } else if (pos != (side > 0)) {
                     pend = xn;
                 }
             }
