@@ -1152,7 +1152,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
         };
         const double gl = left, gr = right;
         const bool lv = true, rv = true;
-        // FP32 opening for the Newton finish: two one-pole model steps on the
+        // FP32 opening for the Newton finish: one-pole model steps on the
         // rescaled FP32 copy (F and F' with c S(x) = K T(y)) give the first
         // FP64 trial point; they move no bracket end (unverified)
         double x0 = NAN, dF0 = NAN;
@@ -1173,7 +1173,12 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                 const double sinv = ldexp(1.0, -ilogb(big));   // 1/s, exact
                 double x = 0.5 * (left + right);
                 double dF32 = NAN, step = INFINITY;
-                for (int t = 0; t < 2; ++t) {
+                // up to 8 steps, until one is shorter than FP32 can resolve
+                // (2^-20 of the distance to the nearest pole): far from the
+                // zero, where a bracket spans orders of magnitude, each step
+                // only about halves the distance, and an FP32 step costs the
+                // FP64 pipe ~1/50 of an FP64 evaluation
+                for (int t = 0; t < 8; ++t) {
                     const float y = (float)(x * sinv);
                     const double xe = s * (double)y;
                     const float2 Tf = secular_sum_f32_d(R, T, sh, sl, sc, i, y);
@@ -1191,6 +1196,7 @@ __device__ EigResult solve_shifted(const P &R, const Team &T, int i, int side,
                     step = fabs(xn - x);
                     dF32 = dF;
                     x = xn;
+                    if (!(step > 0x1p-20 * fabs(x - pole))) break;
                 }
                 x0 = x;
                 // an FP32 step that short (against the distance to the nearest
