@@ -240,3 +240,38 @@ def test_headline_form_batched_slice(ae):
             assert_parity(lam[ks], V[:, ks], o, n, cols=ks,
                           what=f"headline form batch instance {i} (n={n}) sampled")
     B.close()
+
+
+def _fp64_evaluations(ae, kind):
+    n = 8192
+    if kind == "graded4096":
+        d, z, a = W.graded_arrow(4096, seed=1)
+        return ae.arrow_eig(t(d), t(z), a, opts=headline(ae), info=True, vectors=False)["info"]
+    if kind == "graded16384":
+        d, z, a = W.graded_arrow(16384, seed=1)
+        return ae.arrow_eig(t(d), t(z), a, opts=headline(ae), info=True, vectors=False)["info"]
+    if kind == "dpr1":
+        d, u, rho = W.uniform_dpr1(n, seed=3)
+        return ae.dpr1_eig(t(d), t(u), rho, opts=headline(ae), info=True, vectors=False)["info"]
+    if kind == "herm":
+        d, z, a = W.uniform_herm(n, seed=8)
+        return ae.herm_arrow_eig(t(d), t(z, torch.complex128), a, opts=headline(ae), info=True,
+                                 vectors=False)["info"]
+    d, zc, zr, a = W.uniform_nsym(n, seed=10)
+    return ae.nsym_arrow_eig(t(d), t(zc), t(zr), a, opts=headline(ae), info=True,
+                             vectors=False)["info"]
+
+
+@pytest.mark.parametrize("kind", ["graded4096", "graded16384", "dpr1", "herm", "nsym"])
+def test_headline_form_few_fp64_evaluations(ae, kind):
+    # every eigenpair closes in a few FP64 evaluations: the FP32 opening runs
+    # until FP32 can resolve no shorter step, and a step too short for the
+    # model's own rounding is the Newton step (a model step that pointed out
+    # of the bracket once fell back to midpoints: 15-34 evaluations for a few
+    # eigenpairs of each of these workloads, and the launch waited on them)
+    info = _fp64_evaluations(ae, kind)
+    torch.cuda.synchronize()
+    assert info["n_capped"] == 0
+    assert info["max_iter_used"] <= 10, info["max_iter_used"]
+    solves = info["total_iter"] - info["fix_iter"]
+    assert solves <= 1.3 * info["n_reduced"], (solves, info["n_reduced"])
