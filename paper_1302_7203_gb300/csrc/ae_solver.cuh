@@ -868,8 +868,8 @@ __device__ bool fp32_verify(int dir, F64 f64, double l, double r, double &left, 
 //  * when that leaves the bracket, the last such point taken from the side
 //    whose steps do not overshoot, else the midpoint.  The model puts all of
 //    F' beyond kappa on the nearest pole, so near x it is more convex than F:
-//    from the side of the zero away from that pole (F > 0 for side > 0) its
-//    zero lies past F's, from the pole's side (F < 0 for side > 0) short of it.
+//    from the pole's side of the zero (F > 0 for side > 0) its zero lies past
+//    F's, from the far side (F < 0 for side > 0) short of it.
 // Ends lv / rv not yet evaluated in FP64 (from the FP32 phase) are checked
 // after the loop; a failed check is itself a good end on the other side, and
 // the search resumes from the known-good end.  Returns the number of FP64
