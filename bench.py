@@ -276,6 +276,24 @@ def fp64_instructions(n, info, form, terms=None, stored_diff=False):
     return t * (mid + b + evals) + vec
 
 
+def remedy_work(info, terms):
+    """Algorithmic FP64 flops and FP64 lane-instructions of the remedy solves
+    (Remarks 1 and 2), for a roofline over a whole plan whose time includes
+    them: a Remark 1 / 2(b) solve forms its rho-denominator in double-double
+    (20 flops, INSTR_PER_TERM b_dd a term), a Remark 2(a) solve a standard b
+    from the other pole (3 flops, b_std); each remedy's FP64 evaluations
+    (fix_iter, 3 flops and `eval` instructions a term) and its rewritten
+    eigenvector column (6 flops and `vector` instructions a component)."""
+    c = INSTR_PER_TERM
+    n_dd = info["n_dpr1shift"] + info["n_nearzero"]
+    n_op = info["n_otherpole"]
+    flops = terms * (20.0 * n_dd + 3.0 * n_op + 3.0 * info["fix_iter"]) + \
+        6.0 * (terms + 1) * (n_dd + n_op)
+    instr = terms * (c["b_dd"] * n_dd + c["b_std"] * n_op + c["eval"] * info["fix_iter"]) + \
+        c["vector"] * (terms + 1) * (n_dd + n_op)
+    return flops, instr
+
+
 def fp32_flops(n, info, terms=None):
     """Algorithmic FP32 flops of the FP32 and double-float passes (all
     eigenpairs, remedies included)."""
@@ -524,6 +542,11 @@ def extras(arrowhead, W, dev, stream, flush, args, peaks):
                           b_info["total_deriv"],
                           n_mid=b_info["n_mid64"] if FORMS[args.form][0] == 1 else None)
     ins = fp64_instructions(int(round(tm)) + 2, b_info, args.form, terms=tm)
+    # the plan's time includes its remedy stage (about a tenth of this set's
+    # eigenpairs): count that work too
+    rf, ri = remedy_work(b_info, tm)
+    fl += rf
+    ins += ri
     rb = roofline_numbers(fl, ins, fp32_flops(0, b_info, terms=tm), ms / 1e3, peaks)
     # errors: 24 instances spread over the orders (the largest included), 24
     # sampled eigenpairs each
@@ -551,8 +574,12 @@ def extras(arrowhead, W, dev, stream, flush, args, peaks):
                                         "fp64_pipe_busy_implied": rb["fp64_pipe_busy_implied"],
                                         "mixed": rb["mixed"],
                                         "note": "algorithmic FP64 flops of all eigenpairs "
-                                                "(average pass length) over the whole plan's "
-                                                "time, against the measured FP64 rate"},
+                                                "and of the remedy solves (average pass "
+                                                "length) over the whole plan's time, against "
+                                                "the measured FP64 rate"},
+                           "remedies": int(binfo["n_dpr1shift"] + binfo["n_nearzero"] +
+                                           binfo["n_otherpole"]),
+                           "b_double_double": int(binfo["n_ddb"]),
                            "max_err_neps": {**worst, "instances": int(pick.size)},
                            "team_widths": {str(b): arrowhead.lib().ae_team_width(b)
                                            for b in (32, 64, 128, 256, 512)}}

@@ -84,6 +84,16 @@ def test_fp64_instruction_model():
     assert got == (n - 2) * per_terms + c["vector"] * 100 * (n - 1)
 
 
+def test_remedy_work():
+    info = {"n_dpr1shift": 3, "n_nearzero": 1, "n_otherpole": 2, "fix_iter": 9}
+    c = bench.INSTR_PER_TERM
+    fl, ins = bench.remedy_work(info, 50.0)
+    assert fl == 50.0 * (20.0 * 4 + 3.0 * 2 + 3.0 * 9) + 6.0 * 51.0 * 6
+    assert ins == 50.0 * (c["b_dd"] * 4 + c["b_std"] * 2 + c["eval"] * 9) + c["vector"] * 51.0 * 6
+    none = {"n_dpr1shift": 0, "n_nearzero": 0, "n_otherpole": 0, "fix_iter": 0}
+    assert bench.remedy_work(none, 50.0) == (0.0, 0.0)
+
+
 def test_fp32_flops_and_roofline_numbers():
     info = {"n_f32_passes": 10, "n_df_passes": 4}
     f = bench.FP32_FLOPS_PER_TERM
