@@ -7,7 +7,9 @@ or fail).  arrow_eig_noalloc serves them from a static device array instead of
 cudaMallocAsync.  These tests call it through the C ABI and check it against
 arrow_eig at the suite's tolerance (10 n eps64, relative, per eigenvalue and
 eigenvector component), on two calls in a row that reuse the shared array
-with different sizes, so stale contents from the first call would show.
+with different sizes, so stale contents from the first call would show; at
+the largest order the array admits (n = 20928) a sample of eigenvalues is
+checked against the oracle.
 This file is collected last so that a run stopping at the first failure has
 already run every other test.
 """
@@ -159,3 +161,10 @@ def test_noalloc_accepts_its_largest_order(ae):
     lam = lam.cpu().numpy()
     assert info.n_reduced == n and np.all(np.diff(lam) <= 0)
     assert np.all(lam[:-1] >= d) and np.all(d >= lam[1:])   # interlacing (Sec. 1)
+    # and the values themselves: sampled against the oracle at 10 n eps64
+    import oracle
+    ks = np.unique(np.r_[0, 1, n // 3, n // 2, n - 2, n - 1,
+                         np.random.default_rng(44).choice(n, 26, replace=False)])
+    ref = oracle.arrow_eig(d, z, alpha, ks=ks, vectors=False)
+    tol = 10 * n * 2.0 ** -53
+    assert np.all(np.abs(lam[ks] - ref["lam"]) <= tol * np.abs(ref["lam"]))
